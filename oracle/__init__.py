@@ -1,0 +1,259 @@
+"""CPU FP64 oracle for scalar spherical-harmonic synthesis -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  The product path (the CUDA
+library and its Python binding) never imports, links or runs it, and it shares
+no code with that path.
+
+The arithmetic lives in ``sht_oracle.c`` (plain C, OpenMP over rings or m,
+compensated FP64 sums); this module compiles it with gcc, loads it with ctypes
+and wraps it for numpy arrays.  Every function cites the passage of Seljebotn,
+"Wavemoth -- Fast spherical harmonic transforms by butterfly matrix
+compression" (arXiv 1110.4874) that it follows:
+
+* ``healpix_rings`` -- the HEALPix RING grid the paper works on (Sec. 2.2,
+  the grid of Gorski et al. 2005).
+* ``legendre`` -- the normalised associated Legendre functions of Eq. (Y-def),
+  Condon-Shortley phase included, by the one-step recurrence.
+* ``legendre_q`` -- q_m(z_k) of Eq. (legendre-transform).
+* ``phi_synth`` -- the per-ring sum over m of Eq. (sh-baseline) with the ring
+  longitudes of Eq. (phi), as a direct DFT.
+* ``synthesize`` -- Eq. (shdef) at the pixels, i.e. the two stages above.
+* ``phi_adjoint``, ``legendre_adjoint``, ``adjoint`` -- the transpose of the
+  real-linear synthesis map under the plain real inner products (the Y^T of
+  Eq. (datamodel)/(wiener)): (Y^T f)_l0 = sum_p f_p P_l^0(z_p) and
+  (Y^T f)_lm = 2 sum_p f_p P_l^m(z_p) e^{-i m phi_p} for m >= 1.
+
+Parity of every function here is pinned by ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sht_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_LP = ctypes.POINTER(ctypes.c_longlong)
+
+
+def build(force: bool = False) -> str:
+    """Compile sht_oracle.c into a shared library (gcc, -O2, OpenMP).
+
+    ``-ffp-contract=off`` keeps the compensated sums exact (no fused
+    contractions behind the TwoSum steps)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_nalm.restype = ctypes.c_longlong
+            lib.orc_nalm.argtypes = [ctypes.c_int]
+            lib.orc_healpix_rings.argtypes = [ctypes.c_int, _DP, _DP, _IP, _IP, _LP]
+            lib.orc_legendre.restype = None
+            lib.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, _DP]
+            lib.orc_legendre_q.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_int,
+                                           ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_phi_synth.argtypes = [ctypes.c_int, _IP, _IP, ctypes.c_int,
+                                          ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_synth.argtypes = [ctypes.c_int, _DP, _DP, _IP, _IP, ctypes.c_int,
+                                      ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_phi_adjoint.argtypes = [ctypes.c_int, _IP, _IP, ctypes.c_int,
+                                            ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_legendre_adjoint.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_int,
+                                                 ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_adjoint.argtypes = [ctypes.c_int, _DP, _DP, _IP, _IP, ctypes.c_int,
+                                        ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_IP)
+
+
+def max_threads() -> int:
+    """OpenMP threads the oracle uses when ``nthreads=0``."""
+    return int(_load().orc_max_threads())
+
+
+def nalm(lmax: int) -> int:
+    """Number of stored (l, m >= 0) coefficients, (L+1)(L+2)/2."""
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+class Rings:
+    """An iso-latitude ring grid: z, sin(theta), pixels per ring J and the
+    half-pixel flag s (phi_kj = pi (2j + s_k) / J_k)."""
+
+    def __init__(self, z, sinth, J, s):
+        self.z = np.ascontiguousarray(z, dtype=np.float64)
+        self.sinth = np.ascontiguousarray(sinth, dtype=np.float64)
+        self.J = np.ascontiguousarray(J, dtype=np.int32)
+        self.s = np.ascontiguousarray(s, dtype=np.int32)
+        self.start = np.concatenate([[0], np.cumsum(self.J.astype(np.int64))])
+
+    @property
+    def nrings(self) -> int:
+        return int(self.z.shape[0])
+
+    @property
+    def npix(self) -> int:
+        return int(self.start[-1])
+
+    def subset(self, idx) -> "Rings":
+        idx = np.asarray(idx)
+        return Rings(self.z[idx], self.sinth[idx], self.J[idx], self.s[idx])
+
+    def phi(self, k: int) -> np.ndarray:
+        """Longitudes of ring k (Eq. phi)."""
+        j = np.arange(self.J[k])
+        return np.pi * (2 * j + self.s[k]) / self.J[k]
+
+
+def healpix_rings(nside: int) -> Rings:
+    """The 4*nside-1 rings of the HEALPix grid, north to south."""
+    if nside < 1:
+        raise ValueError("nside must be >= 1")
+    nr = 4 * nside - 1
+    z = np.empty(nr)
+    st = np.empty(nr)
+    J = np.empty(nr, dtype=np.int32)
+    s = np.empty(nr, dtype=np.int32)
+    start = np.empty(nr, dtype=np.int64)
+    rc = _load().orc_healpix_rings(nside, _dp(z), _dp(st), _ip(J), _ip(s),
+                                   start.ctypes.data_as(_LP))
+    if rc != 0:
+        raise ValueError("bad nside")
+    return Rings(z, st, J, s)
+
+
+def legendre(m: int, lmax: int, z: float, sinth: float | None = None) -> np.ndarray:
+    """Ptilde_l^m(z) for l = m..lmax (Eq. Y-def, with (-1)^m)."""
+    if sinth is None:
+        sinth = float(np.sqrt((1.0 - z) * (1.0 + z)))
+    out = np.zeros(max(lmax - m + 1, 0))
+    if m <= lmax:
+        _load().orc_legendre(int(m), int(lmax), float(z), float(sinth), _dp(out))
+    return out
+
+
+def _alm2d(alm, lmax):
+    a = np.asarray(alm)
+    if a.ndim == 1:
+        a = a[None, :]
+    if a.shape[-1] != nalm(lmax):
+        raise ValueError("alm has the wrong length for lmax")
+    return np.ascontiguousarray(a.astype(np.complex128)).view(np.float64), a.shape[0]
+
+
+def legendre_q(rings: Rings, lmax: int, alm, nthreads: int = 0) -> np.ndarray:
+    """q_m(z_k) for every ring and m = 0..lmax: complex [nmaps, nrings, lmax+1]."""
+    a, nmaps = _alm2d(alm, lmax)
+    q = np.zeros((nmaps, rings.nrings, lmax + 1), dtype=np.complex128)
+    rc = _load().orc_legendre_q(rings.nrings, _dp(rings.z), _dp(rings.sinth), lmax,
+                                nmaps, _dp(a), _dp(q.view(np.float64)), nthreads)
+    assert rc == 0
+    return q
+
+
+def phi_synth(rings: Rings, lmax: int, q, nthreads: int = 0) -> np.ndarray:
+    """Pixels from q_m(z_k): real [nmaps, npix]."""
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.complex128))
+    if q.ndim == 2:
+        q = q[None]
+    nmaps = q.shape[0]
+    assert q.shape[1:] == (rings.nrings, lmax + 1)
+    out = np.zeros((nmaps, rings.npix))
+    rc = _load().orc_phi_synth(rings.nrings, _ip(rings.J), _ip(rings.s), lmax, nmaps,
+                               _dp(q.view(np.float64)), _dp(out), nthreads)
+    assert rc == 0
+    return out
+
+
+def synthesize(rings: Rings, lmax: int, alm, nthreads: int = 0) -> np.ndarray:
+    """f = Y a at every pixel of ``rings``: real [nmaps, npix] (Eq. shdef)."""
+    a, nmaps = _alm2d(alm, lmax)
+    out = np.zeros((nmaps, rings.npix))
+    rc = _load().orc_synth(rings.nrings, _dp(rings.z), _dp(rings.sinth), _ip(rings.J),
+                           _ip(rings.s), lmax, nmaps, _dp(a), _dp(out), nthreads)
+    assert rc == 0
+    return out
+
+
+def phi_adjoint(rings: Rings, lmax: int, maps, nthreads: int = 0) -> np.ndarray:
+    """F_m(k) = sum_j f_kj e^{-i m phi_kj}: complex [nmaps, nrings, lmax+1]."""
+    f = np.ascontiguousarray(np.atleast_2d(np.asarray(maps, dtype=np.float64)))
+    nmaps = f.shape[0]
+    assert f.shape[1] == rings.npix
+    F = np.zeros((nmaps, rings.nrings, lmax + 1), dtype=np.complex128)
+    rc = _load().orc_phi_adjoint(rings.nrings, _ip(rings.J), _ip(rings.s), lmax, nmaps,
+                                 _dp(f), _dp(F.view(np.float64)), nthreads)
+    assert rc == 0
+    return F
+
+
+def legendre_adjoint(rings: Rings, lmax: int, F, nthreads: int = 0) -> np.ndarray:
+    """a_lm = c_m sum_k Ptilde_l^m(z_k) F_m(k), c_0 = 1, c_m = 2: complex [nmaps, nalm]."""
+    F = np.ascontiguousarray(np.asarray(F, dtype=np.complex128))
+    if F.ndim == 2:
+        F = F[None]
+    nmaps = F.shape[0]
+    alm = np.zeros((nmaps, nalm(lmax)), dtype=np.complex128)
+    rc = _load().orc_legendre_adjoint(rings.nrings, _dp(rings.z), _dp(rings.sinth), lmax,
+                                      nmaps, _dp(F.view(np.float64)),
+                                      _dp(alm.view(np.float64)), nthreads)
+    assert rc == 0
+    return alm
+
+
+def adjoint(rings: Rings, lmax: int, maps, nthreads: int = 0) -> np.ndarray:
+    """Y^T f: complex [nmaps, nalm] (real-inner-product transpose of synthesize)."""
+    f = np.ascontiguousarray(np.atleast_2d(np.asarray(maps, dtype=np.float64)))
+    nmaps = f.shape[0]
+    assert f.shape[1] == rings.npix
+    alm = np.zeros((nmaps, nalm(lmax)), dtype=np.complex128)
+    rc = _load().orc_adjoint(rings.nrings, _dp(rings.z), _dp(rings.sinth), _ip(rings.J),
+                             _ip(rings.s), lmax, nmaps, _dp(f),
+                             _dp(alm.view(np.float64)), nthreads)
+    assert rc == 0
+    return alm
+
+
+def gauss_legendre_rings(nrings: int, nphi: int) -> tuple[Rings, np.ndarray]:
+    """A Gauss-Legendre ring grid (the paper's methods apply to any
+    iso-latitude grid, Sec. 1): nodes/weights from numpy's leggauss,
+    nphi pixels per ring, phi_0 = 0.  Returns (rings, w_k)."""
+    x, w = np.polynomial.legendre.leggauss(nrings)
+    z = x[::-1].copy()
+    w = w[::-1].copy()
+    st = np.sqrt((1.0 - z) * (1.0 + z))
+    return Rings(z, st, np.full(nrings, nphi, np.int32), np.zeros(nrings, np.int32)), w

@@ -1,0 +1,571 @@
+/*
+ * sht_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, obviously-correct CPU reference for scalar spherical
+ * harmonic synthesis on iso-latitude ring grids (HEALPix in particular) and
+ * for its real-inner-product adjoint.  Only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg may load this library; the product path
+ * never does.  It shares no code with the CUDA path.
+ *
+ * What it computes (Seljebotn, "Wavemoth", arXiv 1110.4874):
+ *   - the synthesis sum, Eq. (shdef), evaluated at the pixels (Sec. 2.2);
+ *   - via the separation of sums, Eq. (sh-baseline):
+ *       q_m(z_k) = sum_{l=m}^{L} a_lm Ptilde_l^m(z_k)       (Eq. legendre-transform)
+ *       f(theta_k, phi_kj) = sum_{m=-L}^{L} q_m(z_k) e^{i m phi_kj}
+ *     with q_{-m} = conj(q_m) for a real field (Sec. 2.1, a_{l,-m} = (-1)^m a*_lm)
+ *     and phi_kj = phi_k0 + 2 pi j / J_k (Eq. phi);
+ *   - Ptilde_l^m is the normalised associated Legendre function of Eq. (Y-def),
+ *     with the Condon-Shortley phase (-1)^m.
+ *
+ * Deliberate choices that keep it independent of the fast method:
+ *   - its own ONE-step recurrence in l (the textbook one), not the paper's
+ *     jump-two relation of Eq. (three-term);
+ *   - the recurrence and every sum are carried in double-double (unevaluated
+ *     pairs of FP64 numbers built from error-free transformations: TwoSum,
+ *     and TwoProd by fma), so the oracle's own rounding error stays near
+ *     1e-30 relative instead of growing with l as a plain FP64 recurrence
+ *     does (about 1e-13 at l = 4096 away from the poles, worse near them);
+ *   - recurrence values carry a separate power-of-two exponent, so nothing
+ *     underflows near the poles (sin^m theta reaches 1e-13900 at m = 4096);
+ *   - no even/odd split: every ring is evaluated directly;
+ *   - a direct O(L J) DFT per ring (no FFT), with the angle m*phi reduced
+ *     exactly in integers: phi_kj = pi (2j + s_k) / J_k, so m*phi_kj is
+ *     2 pi n / (2 J_k) with n = m (2j + s_k) mod 2 J_k.
+ *
+ * Ring grid description shared by every routine: nrings rings, ring k has
+ * z[k] = cos(theta_k), sinth[k] = sin(theta_k) (passed separately so the
+ * caller can give it exactly), J[k] pixels and a half-pixel shift flag
+ * s[k] in {0,1}: phi_kj = pi (2 j + s_k) / J_k, j = 0..J_k-1.  Pixel values
+ * of ring k are stored contiguously, rings in the given order.
+ *
+ * a_lm layout: complex128 interleaved (re, im), index m(2L+1-m)/2 + l,
+ * i.e. m-major with l = m..L contiguous; Im a_l0 is ignored.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------- double-double */
+typedef struct { double hi, lo; } dd;
+
+static inline dd two_sum(double a, double b)
+{
+    double s = a + b, bb = s - a;
+    dd r = {s, (a - (s - bb)) + (b - bb)};
+    return r;
+}
+
+static inline dd quick_two_sum(double a, double b)
+{
+    double s = a + b;
+    dd r = {s, b - (s - a)};
+    return r;
+}
+
+static inline dd dd_from(double a) { dd r = {a, 0.0}; return r; }
+
+static inline dd dd_add(dd x, dd y)
+{
+    dd s = two_sum(x.hi, y.hi), t = two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+
+static inline dd dd_neg(dd x) { dd r = {-x.hi, -x.lo}; return r; }
+static inline dd dd_sub(dd x, dd y) { return dd_add(x, dd_neg(y)); }
+
+static inline dd dd_mul(dd x, dd y)
+{
+    double p = x.hi * y.hi;
+    double e = fma(x.hi, y.hi, -p);
+    e += x.hi * y.lo + x.lo * y.hi;
+    return quick_two_sum(p, e);
+}
+
+static inline dd dd_mul_d(dd x, double d)
+{
+    double p = x.hi * d;
+    double e = fma(x.hi, d, -p);
+    e += x.lo * d;
+    return quick_two_sum(p, e);
+}
+
+static inline dd dd_div(dd x, dd y)
+{
+    double q1 = x.hi / y.hi;
+    dd r = dd_sub(x, dd_mul_d(y, q1));
+    double q2 = r.hi / y.hi;
+    r = dd_sub(r, dd_mul_d(y, q2));
+    double q3 = r.hi / y.hi;
+    dd q = quick_two_sum(q1, q2);
+    return dd_add(q, dd_from(q3));
+}
+
+static inline dd dd_sqrt(dd x)
+{
+    if (x.hi <= 0.0) return dd_from(0.0);
+    double s = sqrt(x.hi);
+    double p = s * s;
+    double e = fma(s, s, -p);
+    double r = ((x.hi - p) - e + x.lo) / (2.0 * s);
+    return quick_two_sum(s, r);
+}
+
+static inline dd dd_ldexp(dd x, int e) { dd r = {ldexp(x.hi, e), ldexp(x.lo, e)}; return r; }
+
+/* pi as a double-double */
+static const dd DD_PI = {3.141592653589793116e+00, 1.224646799147353207e-16};
+
+long long orc_nalm(int lmax) { return (long long)(lmax + 1) * (lmax + 2) / 2; }
+
+static long long alm_index(int lmax, int l, int m)
+{
+    return (long long)m * (2 * lmax + 1 - m) / 2 + l;
+}
+
+/* ------------------------------------------------------- HEALPix geometry */
+/*
+ * HEALPix RING scheme (Gorski et al. 2005, the grid the paper targets):
+ *   north polar ring i = 1..N-1 : z = 1 - i^2/(3N^2), J = 4i, phi = pi(2j+1)/(4i)
+ *   belt ring i = N..2N          : z = (4N - 2i)/(3N), J = 4N,
+ *                                  phi = pi(2j+s)/(4N), s = 1 iff (i+N) even
+ *   south ring 4N-i              : mirror of ring i (z -> -z, same J and phi)
+ * Pixels are numbered ring by ring from the north pole.
+ * z and sin(theta) are each formed from exact integers with one division
+ * (and one square root):
+ *   polar: z = (3N^2 - i^2)/(3N^2),  sin^2 = i^2 (6N^2 - i^2) / (9N^4)
+ *   belt : z = (4N - 2i)/(3N),       sin^2 = (2i - N)(7N - 2i) / (9N^2)
+ */
+int orc_healpix_nrings(int nside) { return 4 * nside - 1; }
+
+int orc_healpix_rings(int nside, double *z, double *sinth, int *J, int *s,
+                      long long *start)
+{
+    if (nside < 1) return -1;
+    const long long N = nside;
+    const int nr = 4 * nside - 1;
+    long long pix = 0;
+    for (int r = 1; r <= nr; ++r) {
+        const long long i = r <= 2 * nside ? r : 4 * nside - r;
+        double zi, s2;
+        int Ji, si;
+        if (i < N) {
+            zi = (double)(3 * N * N - i * i) / (double)(3 * N * N);
+            s2 = (double)(i * i * (6 * N * N - i * i)) / (double)(9 * N * N * N * N);
+            Ji = (int)(4 * i);
+            si = 1;
+        } else {
+            zi = (double)(4 * N - 2 * i) / (double)(3 * N);
+            s2 = (double)((2 * i - N) * (7 * N - 2 * i)) / (double)(9 * N * N);
+            Ji = (int)(4 * N);
+            si = ((i + N) % 2 == 0) ? 1 : 0;
+        }
+        const int k = r - 1;
+        z[k] = r > 2 * nside ? -zi : zi;
+        sinth[k] = sqrt(s2);
+        J[k] = Ji;
+        s[k] = si;
+        if (start) start[k] = pix;
+        pix += Ji;
+    }
+    return 0;
+}
+
+/* --------------------------------------------------- Legendre functions */
+/*
+ * Ptilde_l^m(z), l = m..lmax (Eq. Y-def normalisation, Condon-Shortley
+ * phase), by the one-step recurrence
+ *   Ptilde_m^m     = (-1)^m c_m sin^m(theta),
+ *                    c_m^2 = (1/(4 pi)) prod_{i=1}^{m} (2i+1)/(2i)
+ *   Ptilde_{m+1}^m = sqrt(2m+3) z Ptilde_m^m
+ *   Ptilde_l^m     = (z Ptilde_{l-1}^m - b_{l-1} Ptilde_{l-2}^m) / b_l,
+ *   b_l = sqrt((l^2 - m^2)/(4 l^2 - 1)),
+ * all in double-double.  The per-m coefficients are tabulated once in a
+ * plm_table and reused for every ring.
+ */
+typedef struct {
+    int m, lmax;
+    dd cm;            /* c_m                     */
+    dd sq;            /* sqrt(2m+3)              */
+    dd *b;            /* b_l,   l = m+1..lmax    (index l-m) */
+    dd *ib;           /* 1/b_l, l = m+1..lmax    (index l-m) */
+} plm_table;
+
+static void plm_table_init(plm_table *t, int m, int lmax)
+{
+    t->m = m;
+    t->lmax = lmax;
+    dd c2 = dd_div(dd_from(1.0), dd_mul_d(DD_PI, 4.0));
+    for (int i = 1; i <= m; ++i)
+        c2 = dd_mul(c2, dd_div(dd_from(2.0 * i + 1.0), dd_from(2.0 * i)));
+    t->cm = dd_sqrt(c2);
+    t->sq = dd_sqrt(dd_from(2.0 * m + 3.0));
+    int n = lmax - m + 1;
+    t->b = (dd *)malloc(sizeof(dd) * (size_t)(n > 0 ? n : 1));
+    t->ib = (dd *)malloc(sizeof(dd) * (size_t)(n > 0 ? n : 1));
+    for (int l = m + 1; l <= lmax; ++l) {
+        /* (l-m)(l+m) and (2l-1)(2l+1) are exact integers in doubles */
+        dd num = dd_from((double)(l - m) * (double)(l + m));
+        dd den = dd_from((double)(2 * l - 1) * (double)(2 * l + 1));
+        dd b = dd_sqrt(dd_div(num, den));
+        t->b[l - m] = b;
+        t->ib[l - m] = dd_div(dd_from(1.0), b);
+    }
+}
+
+static void plm_table_free(plm_table *t)
+{
+    free(t->b);
+    free(t->ib);
+}
+
+/* mantissa * 2^E with the mantissa's leading double in [0.5, 1) */
+static dd dd_normalise(dd x, int *E)
+{
+    if (x.hi == 0.0) return x;
+    int e;
+    frexp(x.hi, &e);
+    *E += e;
+    return dd_ldexp(x, -e);
+}
+
+/* s^m as (mantissa, exponent) by binary powering */
+static dd dd_pow_scaled(double s, int m, int *E)
+{
+    dd r = dd_from(1.0);
+    int Er = 0, Eb = 0;
+    dd b = dd_normalise(dd_from(s), &Eb);
+    while (m > 0) {
+        if (m & 1) {
+            r = dd_mul(r, b);
+            Er += Eb;
+            r = dd_normalise(r, &Er);
+        }
+        m >>= 1;
+        if (m) {
+            b = dd_mul(b, b);
+            Eb *= 2;
+            b = dd_normalise(b, &Eb);
+        }
+    }
+    *E = Er;
+    return r;
+}
+
+/* Values at one point for l = m..lmax, as double-double (hi, lo arrays). */
+static void plm_eval(const plm_table *t, double z, double sinth, double *ohi, double *olo)
+{
+    const int m = t->m, lmax = t->lmax;
+    int E;
+    dd p0 = dd_pow_scaled(sinth, m, &E);
+    p0 = dd_mul(p0, t->cm);
+    if (m & 1) p0 = dd_neg(p0);
+#define EMIT(idx, v)                                                        \
+    do {                                                                    \
+        if (E == 0) { ohi[idx] = (v).hi; olo[idx] = (v).lo; }               \
+        else { ohi[idx] = ldexp((v).hi, E); olo[idx] = ldexp((v).lo, E); }  \
+    } while (0)
+    EMIT(0, p0);
+    if (m == lmax) return;
+    dd p1 = dd_mul_d(dd_mul(t->sq, p0), z);
+    EMIT(1, p1);
+    for (int l = m + 2; l <= lmax; ++l) {
+        dd a = dd_mul_d(p1, z);
+        dd c = dd_mul(t->b[l - 1 - m], p0);
+        dd p2 = dd_mul(dd_sub(a, c), t->ib[l - m]);
+        p0 = p1;
+        p1 = p2;
+        if (E != 0 && p1.hi != 0.0) {
+            /* bring the pair back to a zero exponent once it is representable */
+            int e;
+            frexp(p1.hi, &e);
+            if (e + E > -900) {
+                p0 = dd_ldexp(p0, E);
+                p1 = dd_ldexp(p1, E);
+                E = 0;
+            } else if (e > 512) {
+                p0 = dd_ldexp(p0, -256);
+                p1 = dd_ldexp(p1, -256);
+                E += 256;
+            }
+        }
+        EMIT(l - m, p1);
+    }
+#undef EMIT
+}
+
+void orc_legendre(int m, int lmax, double z, double sinth, double *out)
+{
+    if (m < 0 || m > lmax) return;
+    plm_table t;
+    plm_table_init(&t, m, lmax);
+    double *lo = (double *)malloc(sizeof(double) * (size_t)(lmax - m + 1));
+    plm_eval(&t, z, sinth, out, lo);
+    for (int i = 0; i <= lmax - m; ++i) out[i] += lo[i];
+    free(lo);
+    plm_table_free(&t);
+}
+
+/* ------------------------------------------------------------ synthesis */
+/*
+ * Legendre stage: q[map][k][m] (complex, interleaved) = sum_l a_lm Ptilde_l^m(z_k)
+ * for m = 0..lmax at each of the given rings (Eq. legendre-transform).
+ * Parallel over m; the sum over l is accumulated in double-double.
+ */
+int orc_legendre_q(int nrings, const double *z, const double *sinth, int lmax,
+                   int nmaps, const double *alm, double *q, int nthreads)
+{
+    if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
+    const long long nalm = orc_nalm(lmax);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *ph = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+        double *pl = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int m = 0; m <= lmax; ++m) {
+            plm_table t;
+            plm_table_init(&t, m, lmax);
+            for (int k = 0; k < nrings; ++k) {
+                plm_eval(&t, z[k], sinth[k], ph, pl);
+                for (int b = 0; b < nmaps; ++b) {
+                    const double *a = alm + 2 * (size_t)nalm * b;
+                    dd re = dd_from(0.0), im = dd_from(0.0);
+                    for (int l = m; l <= lmax; ++l) {
+                        const long long idx = alm_index(lmax, l, m);
+                        const dd P = {ph[l - m], pl[l - m]};
+                        re = dd_add(re, dd_mul_d(P, a[2 * idx]));
+                        if (m > 0) im = dd_add(im, dd_mul_d(P, a[2 * idx + 1]));
+                    }
+                    double *qo = q + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
+                    qo[0] = re.hi + re.lo;
+                    qo[1] = im.hi + im.lo;
+                }
+            }
+            plm_table_free(&t);
+        }
+        free(ph);
+        free(pl);
+    }
+    return 0;
+}
+
+/*
+ * cos and sin of 2 pi n / D for n = 0..D-1 (the exact angles of one ring),
+ * from libm with the integer n folded so that the angle lies in [-pi, pi].
+ */
+static void ring_phase_table(int D, double *c, double *s)
+{
+    for (int n = 0; n < D; ++n) {
+        int k = n;
+        if (2 * k > D) k -= D;
+        double ang = 2.0 * DD_PI.hi * ((double)k / (double)D);
+        c[n] = cos(ang);
+        s[n] = sin(ang);
+    }
+}
+
+/*
+ * Fourier stage: map values from q (Eq. sh-baseline / Eq. phi), as a direct
+ * sum over m for every pixel, accumulated in double-double:
+ *   f_kj = Re q_0 + 2 sum_{m=1}^{L} (Re q_m cos(m phi_kj) - Im q_m sin(m phi_kj)).
+ */
+int orc_phi_synth(int nrings, const int *J, const int *s, int lmax, int nmaps,
+                  const double *q, double *map, int nthreads)
+{
+    if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
+    long long *start = (long long *)malloc(sizeof(long long) * (size_t)(nrings + 1));
+    start[0] = 0;
+    for (int k = 0; k < nrings; ++k) start[k + 1] = start[k] + J[k];
+    const long long npix = start[nrings];
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int k = 0; k < nrings; ++k) {
+            const int Jk = J[k], D = 2 * J[k];
+            double *ct = (double *)malloc(sizeof(double) * (size_t)D);
+            double *st = (double *)malloc(sizeof(double) * (size_t)D);
+            ring_phase_table(D, ct, st);
+            for (int b = 0; b < nmaps; ++b) {
+                const double *qk = q + 2 * (((size_t)b * nrings + k) * (lmax + 1));
+                double *out = map + (size_t)b * npix + start[k];
+                for (int j = 0; j < Jk; ++j) {
+                    const long long step = 2LL * j + s[k];   /* m*phi = 2 pi m step / D */
+                    dd acc = dd_from(qk[0]);
+                    long long n = 0;
+                    for (int m = 1; m <= lmax; ++m) {
+                        n = (n + step) % D;
+                        acc = dd_add(acc, dd_mul_d(dd_from(2.0 * qk[2 * m]), ct[n]));
+                        acc = dd_add(acc, dd_mul_d(dd_from(-2.0 * qk[2 * m + 1]), st[n]));
+                    }
+                    out[j] = acc.hi + acc.lo;
+                }
+            }
+            free(ct);
+            free(st);
+        }
+    }
+    free(start);
+    return 0;
+}
+
+/* Full synthesis: Legendre stage then Fourier stage. */
+int orc_synth(int nrings, const double *z, const double *sinth, const int *J,
+              const int *s, int lmax, int nmaps, const double *alm, double *map,
+              int nthreads)
+{
+    size_t nq = 2 * (size_t)nmaps * nrings * (lmax + 1);
+    double *q = (double *)malloc(sizeof(double) * (nq ? nq : 1));
+    if (!q) return -2;
+    int rc = orc_legendre_q(nrings, z, sinth, lmax, nmaps, alm, q, nthreads);
+    if (rc == 0) rc = orc_phi_synth(nrings, J, s, lmax, nmaps, q, map, nthreads);
+    free(q);
+    return rc;
+}
+
+/* -------------------------------------------------------------- adjoint */
+/*
+ * Fourier-stage adjoint: F[map][k][m] = sum_j f_kj e^{-i m phi_kj}, m = 0..L.
+ */
+int orc_phi_adjoint(int nrings, const int *J, const int *s, int lmax, int nmaps,
+                    const double *map, double *F, int nthreads)
+{
+    if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
+    long long *start = (long long *)malloc(sizeof(long long) * (size_t)(nrings + 1));
+    start[0] = 0;
+    for (int k = 0; k < nrings; ++k) start[k + 1] = start[k] + J[k];
+    const long long npix = start[nrings];
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int k = 0; k < nrings; ++k) {
+            const int Jk = J[k], D = 2 * J[k];
+            double *ct = (double *)malloc(sizeof(double) * (size_t)D);
+            double *st = (double *)malloc(sizeof(double) * (size_t)D);
+            ring_phase_table(D, ct, st);
+            for (int b = 0; b < nmaps; ++b) {
+                const double *f = map + (size_t)b * npix + start[k];
+                double *Fk = F + 2 * (((size_t)b * nrings + k) * (lmax + 1));
+                for (int m = 0; m <= lmax; ++m) {
+                    dd re = dd_from(0.0), im = dd_from(0.0);
+                    for (int j = 0; j < Jk; ++j) {
+                        long long n = ((long long)m * (2LL * j + s[k])) % D;
+                        re = dd_add(re, dd_mul_d(dd_from(f[j]), ct[n]));
+                        im = dd_add(im, dd_mul_d(dd_from(-f[j]), st[n]));
+                    }
+                    Fk[2 * m] = re.hi + re.lo;
+                    Fk[2 * m + 1] = im.hi + im.lo;
+                }
+            }
+            free(ct);
+            free(st);
+        }
+    }
+    free(start);
+    return 0;
+}
+
+/*
+ * Legendre-stage adjoint: alm[l,m] = c_m sum_k Ptilde_l^m(z_k) F_m(k), with
+ * c_0 = 1 (and Im a_l0 = 0) and c_m = 2 for m >= 1.  Together with the
+ * Fourier-stage adjoint this is the transpose of the real-linear synthesis
+ * map (Re a_lm, Im a_lm) -> f under the plain real inner products, i.e.
+ *   (Y^T f)_l0 = sum_p f_p Ptilde_l^0(z_p),
+ *   (Y^T f)_lm = 2 sum_p f_p Ptilde_l^m(z_p) e^{-i m phi_p}   (m >= 1);
+ * it is the Y^dagger of Eq. (wiener) up to the factor 2 for m >= 1.
+ */
+int orc_legendre_adjoint(int nrings, const double *z, const double *sinth,
+                         int lmax, int nmaps, const double *F, double *alm,
+                         int nthreads)
+{
+    if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
+    const long long nalm = orc_nalm(lmax);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *ph = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+        double *pl = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+        dd *acc = (dd *)malloc(sizeof(dd) * 2 * (size_t)(lmax + 1) * nmaps);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int m = 0; m <= lmax; ++m) {
+            const int n = lmax - m + 1;
+            for (size_t i = 0; i < 2 * (size_t)n * nmaps; ++i) acc[i] = dd_from(0.0);
+            plm_table t;
+            plm_table_init(&t, m, lmax);
+            for (int k = 0; k < nrings; ++k) {
+                plm_eval(&t, z[k], sinth[k], ph, pl);
+                for (int b = 0; b < nmaps; ++b) {
+                    const double *Fk = F + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
+                    dd *ab = acc + 2 * (size_t)n * b;
+                    for (int i = 0; i < n; ++i) {
+                        const dd P = {ph[i], pl[i]};
+                        ab[2 * i] = dd_add(ab[2 * i], dd_mul_d(P, Fk[0]));
+                        ab[2 * i + 1] = dd_add(ab[2 * i + 1], dd_mul_d(P, Fk[1]));
+                    }
+                }
+            }
+            plm_table_free(&t);
+            const double cm = m == 0 ? 1.0 : 2.0;
+            for (int b = 0; b < nmaps; ++b) {
+                dd *ab = acc + 2 * (size_t)n * b;
+                for (int i = 0; i < n; ++i) {
+                    const long long idx = alm_index(lmax, m + i, m);
+                    double *o = alm + 2 * ((size_t)nalm * b + idx);
+                    o[0] = cm * (ab[2 * i].hi + ab[2 * i].lo);
+                    o[1] = m == 0 ? 0.0 : cm * (ab[2 * i + 1].hi + ab[2 * i + 1].lo);
+                }
+            }
+        }
+        free(ph);
+        free(pl);
+        free(acc);
+    }
+    return 0;
+}
+
+/* Full adjoint: Fourier-stage adjoint then Legendre-stage adjoint. */
+int orc_adjoint(int nrings, const double *z, const double *sinth, const int *J,
+                const int *s, int lmax, int nmaps, const double *map,
+                double *alm, int nthreads)
+{
+    size_t nF = 2 * (size_t)nmaps * nrings * (lmax + 1);
+    double *F = (double *)malloc(sizeof(double) * (nF ? nF : 1));
+    if (!F) return -2;
+    int rc = orc_phi_adjoint(nrings, J, s, lmax, nmaps, map, F, nthreads);
+    if (rc == 0) rc = orc_legendre_adjoint(nrings, z, sinth, lmax, nmaps, F, alm, nthreads);
+    free(F);
+    return rc;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

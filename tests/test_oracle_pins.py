@@ -1,0 +1,361 @@
+"""Pins of the CPU oracle against facts fixed by the paper and the mathematics.
+
+Nothing here compares the oracle with itself: each test checks it against a
+closed form, a library routine (scipy's spherical harmonics, numpy's
+Gauss-Legendre nodes), a printed formula of the paper (the jump-two
+coefficients of Eq. three-term), or an exact identity of the grid or of
+linear algebra.  A dropped term, a wrong sign or index, a transposed operand
+or a wrong factor in any oracle routine fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from fractions import Fraction
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _alm_index(lmax, l, m):
+    return m * (2 * lmax + 1 - m) // 2 + l
+
+
+def _random_alm(lmax, nmaps, seed):
+    rng = np.random.default_rng(seed)
+    n = oracle.nalm(lmax)
+    a = rng.standard_normal((nmaps, n)) + 1j * rng.standard_normal((nmaps, n))
+    for l in range(lmax + 1):
+        a[:, _alm_index(lmax, l, 0)] = a[:, _alm_index(lmax, l, 0)].real
+    return a
+
+
+# ------------------------------------------------------------ grid geometry
+def _healpix_pix2ang(nside, p):
+    """Pixel centre (z, phi) of RING pixel p from the pixel-index formulas of
+    Gorski et al. 2005 (a per-pixel route, independent of the oracle's
+    per-ring loop)."""
+    npix = 12 * nside * nside
+    ncap = 2 * nside * (nside - 1)
+    if p < ncap:                                   # north polar cap
+        i = (1 + math.isqrt(1 + 2 * p)) // 2
+        j = p + 1 - 2 * i * (i - 1)
+        return 1 - i * i / (3 * nside * nside), (j - 0.5) * (math.pi / 2) / i
+    if p < npix - ncap:                            # equatorial belt
+        q = p - ncap
+        i = q // (4 * nside) + nside
+        j = q % (4 * nside) + 1
+        fodd = 1.0 if (i + nside) % 2 else 0.5
+        return (4 * nside - 2 * i) / (3 * nside), (j - fodd) * math.pi / (2 * nside)
+    q = npix - p - 1                               # south polar cap (mirror)
+    i = (1 + math.isqrt(1 + 2 * q)) // 2
+    j = 4 * i + 1 - (q + 1 - 2 * i * (i - 1))
+    return -(1 - i * i / (3 * nside * nside)), (j - 0.5) * (math.pi / 2) / i
+
+
+def _expand(rings):
+    zs, phis = [], []
+    for k in range(rings.nrings):
+        zs.append(np.full(rings.J[k], rings.z[k]))
+        phis.append(rings.phi(k))
+    return np.concatenate(zs), np.concatenate(phis)
+
+
+def test_healpix_nside1_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "healpix_nside1_pixel_centres.txt"))
+            if l.strip() and not l.startswith("#")]
+    z, phi = _expand(oracle.healpix_rings(1))
+    assert len(rows) == 12 == z.size
+    for r in rows:
+        p = int(r[0])
+        assert z[p] == pytest.approx(int(r[1]) / int(r[2]), abs=1e-15)
+        assert phi[p] == pytest.approx(math.pi * int(r[3]) / int(r[4]), abs=1e-15)
+
+
+@pytest.mark.parametrize("nside", [1, 2, 3, 4, 7, 16, 33])
+def test_healpix_rings_match_pixel_formulas(nside):
+    rings = oracle.healpix_rings(nside)
+    assert rings.nrings == 4 * nside - 1
+    assert rings.npix == 12 * nside * nside
+    z, phi = _expand(rings)
+    for p in range(rings.npix):
+        zp, php = _healpix_pix2ang(nside, p)
+        assert z[p] == pytest.approx(zp, abs=1e-15)
+        assert phi[p] == pytest.approx(php, abs=1e-13)
+    # sin(theta) is given exactly, consistent with z
+    np.testing.assert_allclose(rings.sinth ** 2 + rings.z ** 2, 1.0, atol=1e-15)
+    # rings are symmetric about the equator
+    np.testing.assert_array_equal(rings.J, rings.J[::-1])
+    np.testing.assert_allclose(rings.z, -rings.z[::-1], atol=0)
+
+
+# ----------------------------------------------------- Legendre functions
+def _closed_forms():
+    out = []
+    for line in open(os.path.join(GOLDEN, "legendre_closed_forms.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        l, m, sign, C, poly = line.split()
+        out.append((int(l), int(m), int(sign), float(Fraction(C)), poly))
+    return out
+
+
+def test_legendre_closed_forms():
+    forms = _closed_forms()
+    assert len(forms) == 10
+    for z in np.linspace(-0.999, 0.999, 37):
+        s = math.sqrt((1 - z) * (1 + z))
+        for l, m, sign, C, poly in forms:
+            want = sign * math.sqrt(C / math.pi) * eval(poly, {"z": z, "s": s})
+            got = oracle.legendre(m, 3, z, s)[l - m]
+            assert got == pytest.approx(want, rel=1e-14, abs=1e-15), (l, m, z)
+
+
+def test_legendre_matches_scipy():
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        m = int(rng.integers(0, 150))
+        lmax = m + int(rng.integers(0, 150))
+        z = float(rng.uniform(-0.99, 0.99))
+        got = oracle.legendre(m, lmax, z)
+        ls = np.arange(m, lmax + 1)
+        want = sp.sph_harm_y(ls, m, math.acos(z), 0.0).real
+        scale = max(np.abs(want).max(), 1e-300)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * scale)
+
+
+def test_legendre_diagonal_log_closed_form():
+    """|Ptilde_m^m| = sqrt((2m+1)/(4pi) (2m)!/(4^m m!^2)) sin^m(theta), in
+    logarithms, far into the range where sin^m underflows in doubles."""
+    nside = 2048
+    rings = oracle.healpix_rings(nside)
+    for k in [0, 1, 5, 40, 300, 2047]:
+        z, st = rings.z[k], rings.sinth[k]
+        for m in [1, 10, 100, 700, 1500, 4000]:
+            v = oracle.legendre(m, m, z, st)[0]
+            logv = 0.5 * (math.log((2 * m + 1) / (4 * math.pi)) + math.lgamma(2 * m + 1)
+                          - 2 * math.lgamma(m + 1) - m * math.log(4)) + m * math.log(st)
+            if logv < math.log(1e-290):
+                assert abs(v) < 1e-280
+                continue
+            assert math.log(abs(v)) == pytest.approx(logv, abs=1e-11)
+            assert (v < 0) == (m % 2 == 1)     # Condon-Shortley sign
+
+
+@pytest.mark.parametrize("lmax", [64, 1024, 4096])
+def test_addition_theorem(lmax):
+    """P_l^0(z)^2 + 2 sum_{m>=1} P_l^m(z)^2 = (2l+1)/(4 pi) for every l, at
+    near-pole, mid and equatorial z (including the first HEALPix ring at
+    Nside=2048, where most of the terms underflow).
+
+    A pair of doubles (z, sin theta) is never exactly on the unit circle: a
+    relative mismatch d <= 2^-53 in sin(theta) moves Ptilde_l^m by m*d, so
+    the identity can only hold to about 2*L*2^-53 where large m contribute
+    (mid latitudes).  Near the poles (only small m contribute) and on the
+    equator (z = 0, sin = 1 exactly) it must hold to a few ulp: a plain FP64
+    one-step recurrence misses it by 1.5e-11 at l = 4096 next to the pole."""
+    cases = [(1 - 1 / (3 * 2048 ** 2), 1e-14), (1 - 1 / (3 * 64 ** 2), 1e-14), (0.0, 1e-14),
+             (0.93, None), (0.5, None), (0.1, None), (-0.77, None)]
+    for z, tol in cases:
+        st = math.sqrt((1 - z) * (1 + z))
+        acc = np.zeros(lmax + 1)
+        for m in range(lmax + 1):
+            p = oracle.legendre(m, lmax, z, st)
+            acc[m:] += (1.0 if m == 0 else 2.0) * p * p
+        want = (2 * np.arange(lmax + 1) + 1) / (4 * math.pi)
+        rtol = tol if tol is not None else 2.5 * lmax * 2.0 ** -53 + 1e-14
+        np.testing.assert_allclose(acc, want, rtol=rtol)
+
+
+def test_legendre_satisfies_paper_jump_two_recurrence():
+    """The oracle's one-step values obey the paper's jump-two relation,
+    Eq. (three-term): P_{l+2} = ((z^2 - d_l)/c_l) P_l - (c_{l-2}/c_l) P_{l-2},
+    with c_l^m and d_l^m as printed in the appendix."""
+    def c(l, m):
+        return math.sqrt((l - m + 1) * (l - m + 2) * (l + m + 1) * (l + m + 2)
+                         / ((2 * l + 1) * (2 * l + 3) ** 2 * (2 * l + 5)))
+
+    def d(l, m):
+        return (2 * l * (l + 1) - 2 * m * m - 1) / ((2 * l - 1) * (2 * l + 3))
+
+    rng = np.random.default_rng(11)
+    for _ in range(30):
+        m = int(rng.integers(0, 300))
+        lmax = m + 60
+        z = float(rng.uniform(-0.95, 0.95))
+        p = oracle.legendre(m, lmax, z)
+        for l in range(m + 2, lmax - 1):
+            lhs = p[l + 2 - m]
+            rhs = (z * z - d(l, m)) / c(l, m) * p[l - m] - c(l - 2, m) / c(l, m) * p[l - 2 - m]
+            assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
+        # self-starting chains: c_{m-2} = c_{m-1} = 0 would be the missing terms
+        rhs = (z * z - d(m, m)) / c(m, m) * p[0]
+        assert p[2] == pytest.approx(rhs, rel=1e-12, abs=1e-14)
+
+
+# --------------------------------------------------------------- synthesis
+def test_single_mode_inputs():
+    """a_lm = 1 gives f = 2 P_l^m(z) cos(m phi); a_lm = i gives -2 P sin(m phi);
+    m = 0 gives P_l^0(z) (Eq. shdef with a_{l,-m} = (-1)^m a*_lm)."""
+    sp = pytest.importorskip("scipy.special")
+    nside, lmax = 4, 9
+    rings = oracle.healpix_rings(nside)
+    z, phi = _expand(rings)
+    th = np.arccos(z)
+    for (l, m) in [(0, 0), (3, 0), (5, 2), (7, 7), (9, 4), (8, 1)]:
+        for val in [1.0, 1j]:
+            if m == 0 and val == 1j:
+                continue
+            a = np.zeros(oracle.nalm(lmax), complex)
+            a[_alm_index(lmax, l, m)] = val
+            f = oracle.synthesize(rings, lmax, a)[0]
+            P = sp.sph_harm_y(l, m, th, 0.0).real
+            if m == 0:
+                want = P
+            elif val == 1.0:
+                want = 2 * P * np.cos(m * phi)
+            else:
+                want = -2 * P * np.sin(m * phi)
+            np.testing.assert_allclose(f, want, atol=1e-14)
+
+
+def test_synthesis_brute_force_vs_scipy():
+    """Eq. (shdef) summed pixel by pixel with scipy's Y_lm over all m = -L..L."""
+    sp = pytest.importorskip("scipy.special")
+    nside, lmax = 4, 8
+    rings = oracle.healpix_rings(nside)
+    z, phi = _expand(rings)
+    th = np.arccos(z)
+    a = _random_alm(lmax, 2, 5)
+    got = oracle.synthesize(rings, lmax, a)
+    for b in range(2):
+        want = np.zeros(z.size, complex)
+        for l in range(lmax + 1):
+            for m in range(-l, l + 1):
+                alm = a[b, _alm_index(lmax, l, abs(m))]
+                if m < 0:
+                    alm = (-1) ** m * np.conj(alm)
+                want += alm * sp.sph_harm_y(l, m, th, phi)
+        assert np.abs(want.imag).max() < 1e-13
+        np.testing.assert_allclose(got[b], want.real, atol=1e-13)
+
+
+def test_mirror_parity():
+    """Eq. (q-even-odd2): only-even (l-m) inputs are mirror-symmetric, only-odd
+    inputs antisymmetric; the odd part vanishes on the equator."""
+    nside, lmax = 8, 20
+    rings = oracle.healpix_rings(nside)
+    a = _random_alm(lmax, 1, 3)[0]
+    par = np.array([(l - m) % 2 for m in range(lmax + 1) for l in range(m, lmax + 1)])
+    for p, sign in [(0, 1.0), (1, -1.0)]:
+        f = oracle.synthesize(rings, lmax, np.where(par == p, a, 0))[0]
+        for k in range(2 * nside - 1):
+            kk = rings.nrings - 1 - k
+            np.testing.assert_allclose(f[rings.start[k]:rings.start[k + 1]],
+                                       sign * f[rings.start[kk]:rings.start[kk + 1]], atol=1e-13)
+        if p == 1:
+            e = 2 * nside - 1
+            assert np.abs(f[rings.start[e]:rings.start[e + 1]]).max() < 1e-14
+
+
+def test_ring_phi_orthogonality():
+    """On a HEALPix ring, sum_j e^{i(m-m')phi_j} = 0 for 0 < |m-m'| < J and
+    J for m = m' (exact), so the Fourier-stage adjoint of a single-m q returns
+    J q_m at m and 0 elsewhere (m + m' < J)."""
+    nside, lmax = 8, 15
+    rings = oracle.healpix_rings(nside)
+    for k in [2, 7, 12]:
+        one = rings.subset([k])
+        J = int(one.J[0])
+        for m0 in range(1, J // 2):
+            if m0 > lmax:
+                break
+            q = np.zeros((1, 1, lmax + 1), complex)
+            q[0, 0, m0] = 0.3 - 0.7j
+            F = oracle.phi_adjoint(one, lmax, oracle.phi_synth(one, lmax, q))[0, 0]
+            for m in range(1, lmax + 1):
+                if m + m0 >= J or abs(m - m0) >= J:
+                    continue
+                want = J * q[0, 0, m0] if m == m0 else 0.0
+                assert abs(F[m] - want) < 1e-12
+
+
+def test_gauss_legendre_quadrature_orthogonality():
+    """On a Gauss-Legendre ring grid (nodes/weights from numpy) with L+1 rings,
+    2 pi sum_k w_k P_l^m(z_k) P_l'^m(z_k) = delta_ll' exactly for l, l' <= L."""
+    lmax = 16
+    rings, w = oracle.gauss_legendre_rings(lmax + 1, 2 * lmax + 1)
+    for m in range(lmax + 1):
+        P = np.array([oracle.legendre(m, lmax, z, s) for z, s in zip(rings.z, rings.sinth)])
+        G = 2 * math.pi * (P.T * w) @ P
+        np.testing.assert_allclose(G, np.eye(lmax - m + 1), atol=2e-14)
+
+
+def test_gauss_legendre_discrete_analysis_roundtrip():
+    """Quadrature weights times the adjoint invert synthesis exactly on a
+    Gauss-Legendre grid with J >= 2L+1: Y^T(W Y a) = a for m = 0 (real part)
+    and 2 a for m >= 1 (Eq. sh-forward-quadrature with the real-inner-product
+    adjoint)."""
+    lmax = 12
+    rings, w = oracle.gauss_legendre_rings(lmax + 1, 2 * lmax + 3)
+    a = _random_alm(lmax, 2, 9)
+    f = oracle.synthesize(rings, lmax, a)
+    wp = np.repeat(2 * math.pi * w / rings.J, rings.J)
+    back = oracle.adjoint(rings, lmax, f * wp)
+    want = a.copy()
+    mcol = np.array([m for m in range(lmax + 1) for _ in range(m, lmax + 1)])
+    want[:, mcol > 0] *= 2
+    np.testing.assert_allclose(back, want, atol=2e-13)
+
+
+def test_adjoint_dot_product_identity():
+    """<Y a, f> = <a, Y^T f> with real inner products over (Re, Im) a_lm."""
+    nside, lmax = 8, 16
+    rings = oracle.healpix_rings(nside)
+    a = _random_alm(lmax, 3, 21)
+    f = np.random.default_rng(22).standard_normal((3, rings.npix))
+    lhs = np.sum(oracle.synthesize(rings, lmax, a) * f)
+    at = oracle.adjoint(rings, lmax, f)
+    rhs = np.sum(a.real * at.real + a.imag * at.imag)
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    # Im a_l0 is ignored by synthesis, so the adjoint's Im a_l0 is zero
+    m0 = [_alm_index(lmax, l, 0) for l in range(lmax + 1)]
+    assert np.all(at[:, m0].imag == 0)
+
+
+def test_adjoint_is_explicit_transpose():
+    """Dense Y from synthesising every real unit coefficient; Y^T applied to
+    random maps must equal the oracle's adjoint."""
+    nside, lmax = 2, 5
+    rings = oracle.healpix_rings(nside)
+    n = oracle.nalm(lmax)
+    cols, which = [], []
+    for i in range(n):
+        for part in (1.0, 1j):
+            e = np.zeros(n, complex)
+            e[i] = part
+            cols.append(oracle.synthesize(rings, lmax, e)[0])
+            which.append((i, part))
+    Y = np.array(cols).T                      # npix x 2n
+    f = np.random.default_rng(4).standard_normal((2, rings.npix))
+    yt = f @ Y                                # 2 x 2n
+    at = oracle.adjoint(rings, lmax, f)
+    for c, (i, part) in enumerate(which):
+        got = at[:, i].real if part == 1.0 else at[:, i].imag
+        np.testing.assert_allclose(got, yt[:, c], atol=1e-13)
+
+
+def test_legendre_stage_matches_full_synthesis_on_ring_subset():
+    """Evaluating a subset of rings gives exactly those rings of the full map."""
+    nside, lmax = 8, 16
+    rings = oracle.healpix_rings(nside)
+    a = _random_alm(lmax, 2, 31)
+    full = oracle.synthesize(rings, lmax, a)
+    idx = [0, 5, 15, 16, 30]
+    sub = rings.subset(idx)
+    part = oracle.synthesize(sub, lmax, a)
+    want = np.concatenate([full[:, rings.start[k]:rings.start[k + 1]] for k in idx], axis=1)
+    np.testing.assert_array_equal(part, want)
