@@ -71,22 +71,26 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.orc_nalm.restype = ctypes.c_longlong
             lib.orc_nalm.argtypes = [ctypes.c_int]
-            lib.orc_healpix_rings.argtypes = [ctypes.c_int, _DP, _DP, _IP, _IP, _LP]
+            lib.orc_healpix_rings.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, _IP, _IP, _LP]
+            lib.orc_sin_from_cos.restype = None
+            lib.orc_sin_from_cos.argtypes = [ctypes.c_int, _DP, _DP, _DP]
             lib.orc_legendre.restype = None
             lib.orc_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, _DP]
-            lib.orc_legendre_q.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_int,
+            lib.orc_legendre_q.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int,
                                            ctypes.c_int, _DP, _DP, ctypes.c_int]
             lib.orc_phi_synth.argtypes = [ctypes.c_int, _IP, _IP, ctypes.c_int,
                                           ctypes.c_int, _DP, _DP, ctypes.c_int]
-            lib.orc_synth.argtypes = [ctypes.c_int, _DP, _DP, _IP, _IP, ctypes.c_int,
-                                      ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_synth.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, _IP, _IP,
+                                      ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int]
             lib.orc_phi_adjoint.argtypes = [ctypes.c_int, _IP, _IP, ctypes.c_int,
                                             ctypes.c_int, _DP, _DP, ctypes.c_int]
-            lib.orc_legendre_adjoint.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_int,
-                                                 ctypes.c_int, _DP, _DP, ctypes.c_int]
-            lib.orc_adjoint.argtypes = [ctypes.c_int, _DP, _DP, _IP, _IP, ctypes.c_int,
-                                        ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_legendre_adjoint.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP,
+                                                 ctypes.c_int, ctypes.c_int, _DP, _DP,
+                                                 ctypes.c_int]
+            lib.orc_adjoint.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, _IP, _IP,
+                                        ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -111,12 +115,24 @@ def nalm(lmax: int) -> int:
 
 
 class Rings:
-    """An iso-latitude ring grid: z, sin(theta), pixels per ring J and the
-    half-pixel flag s (phi_kj = pi (2j + s_k) / J_k)."""
+    """An iso-latitude ring grid: z = cos(theta) and sin(theta) per ring, each
+    as a double-double pair (hi + lo), pixels per ring J and the half-pixel
+    flag s (phi_kj = pi (2j + s_k) / J_k).  If the low parts are omitted, z is
+    taken as exact and sin(theta) = sqrt((1-z)(1+z)) is formed in
+    double-double."""
 
-    def __init__(self, z, sinth, J, s):
+    def __init__(self, z, sinth, J, s, zlo=None, sinlo=None):
         self.z = np.ascontiguousarray(z, dtype=np.float64)
-        self.sinth = np.ascontiguousarray(sinth, dtype=np.float64)
+        self.zlo = (np.zeros_like(self.z) if zlo is None
+                    else np.ascontiguousarray(zlo, dtype=np.float64))
+        if sinth is None or sinlo is None:
+            st = np.empty_like(self.z)
+            sl = np.empty_like(self.z)
+            _load().orc_sin_from_cos(self.z.size, _dp(self.z), _dp(st), _dp(sl))
+            self.sinth, self.sinlo = st, sl
+        else:
+            self.sinth = np.ascontiguousarray(sinth, dtype=np.float64)
+            self.sinlo = np.ascontiguousarray(sinlo, dtype=np.float64)
         self.J = np.ascontiguousarray(J, dtype=np.int32)
         self.s = np.ascontiguousarray(s, dtype=np.int32)
         self.start = np.concatenate([[0], np.cumsum(self.J.astype(np.int64))])
@@ -131,12 +147,16 @@ class Rings:
 
     def subset(self, idx) -> "Rings":
         idx = np.asarray(idx)
-        return Rings(self.z[idx], self.sinth[idx], self.J[idx], self.s[idx])
+        return Rings(self.z[idx], self.sinth[idx], self.J[idx], self.s[idx],
+                     self.zlo[idx], self.sinlo[idx])
 
     def phi(self, k: int) -> np.ndarray:
         """Longitudes of ring k (Eq. phi)."""
         j = np.arange(self.J[k])
         return np.pi * (2 * j + self.s[k]) / self.J[k]
+
+    def _geo(self):
+        return (_dp(self.z), _dp(self.zlo), _dp(self.sinth), _dp(self.sinlo))
 
 
 def healpix_rings(nside: int) -> Rings:
@@ -144,25 +164,33 @@ def healpix_rings(nside: int) -> Rings:
     if nside < 1:
         raise ValueError("nside must be >= 1")
     nr = 4 * nside - 1
-    z = np.empty(nr)
-    st = np.empty(nr)
+    z, zl, st, sl = (np.empty(nr) for _ in range(4))
     J = np.empty(nr, dtype=np.int32)
     s = np.empty(nr, dtype=np.int32)
     start = np.empty(nr, dtype=np.int64)
-    rc = _load().orc_healpix_rings(nside, _dp(z), _dp(st), _ip(J), _ip(s),
+    rc = _load().orc_healpix_rings(nside, _dp(z), _dp(zl), _dp(st), _dp(sl), _ip(J), _ip(s),
                                    start.ctypes.data_as(_LP))
     if rc != 0:
         raise ValueError("bad nside")
-    return Rings(z, st, J, s)
+    return Rings(z, st, J, s, zl, sl)
 
 
-def legendre(m: int, lmax: int, z: float, sinth: float | None = None) -> np.ndarray:
-    """Ptilde_l^m(z) for l = m..lmax (Eq. Y-def, with (-1)^m)."""
-    if sinth is None:
-        sinth = float(np.sqrt((1.0 - z) * (1.0 + z)))
+def legendre(m: int, lmax: int, z: float, sinth: float | None = None,
+             zlo: float = 0.0, sinlo: float | None = None) -> np.ndarray:
+    """Ptilde_l^m(z) for l = m..lmax (Eq. Y-def, with (-1)^m).  Without
+    sin(theta), it is formed from z in double-double."""
+    if sinth is None or sinlo is None:
+        zz = np.array([z], dtype=np.float64)
+        st, sl = np.empty(1), np.empty(1)
+        _load().orc_sin_from_cos(1, _dp(zz), _dp(st), _dp(sl))
+        if sinth is None:
+            sinth, sinlo = float(st[0]), float(sl[0])
+        else:
+            sinlo = 0.0
     out = np.zeros(max(lmax - m + 1, 0))
     if m <= lmax:
-        _load().orc_legendre(int(m), int(lmax), float(z), float(sinth), _dp(out))
+        _load().orc_legendre(int(m), int(lmax), float(z), float(zlo), float(sinth),
+                             float(sinlo), _dp(out))
     return out
 
 
@@ -179,7 +207,7 @@ def legendre_q(rings: Rings, lmax: int, alm, nthreads: int = 0) -> np.ndarray:
     """q_m(z_k) for every ring and m = 0..lmax: complex [nmaps, nrings, lmax+1]."""
     a, nmaps = _alm2d(alm, lmax)
     q = np.zeros((nmaps, rings.nrings, lmax + 1), dtype=np.complex128)
-    rc = _load().orc_legendre_q(rings.nrings, _dp(rings.z), _dp(rings.sinth), lmax,
+    rc = _load().orc_legendre_q(rings.nrings, *rings._geo(), lmax,
                                 nmaps, _dp(a), _dp(q.view(np.float64)), nthreads)
     assert rc == 0
     return q
@@ -203,7 +231,7 @@ def synthesize(rings: Rings, lmax: int, alm, nthreads: int = 0) -> np.ndarray:
     """f = Y a at every pixel of ``rings``: real [nmaps, npix] (Eq. shdef)."""
     a, nmaps = _alm2d(alm, lmax)
     out = np.zeros((nmaps, rings.npix))
-    rc = _load().orc_synth(rings.nrings, _dp(rings.z), _dp(rings.sinth), _ip(rings.J),
+    rc = _load().orc_synth(rings.nrings, *rings._geo(), _ip(rings.J),
                            _ip(rings.s), lmax, nmaps, _dp(a), _dp(out), nthreads)
     assert rc == 0
     return out
@@ -228,7 +256,7 @@ def legendre_adjoint(rings: Rings, lmax: int, F, nthreads: int = 0) -> np.ndarra
         F = F[None]
     nmaps = F.shape[0]
     alm = np.zeros((nmaps, nalm(lmax)), dtype=np.complex128)
-    rc = _load().orc_legendre_adjoint(rings.nrings, _dp(rings.z), _dp(rings.sinth), lmax,
+    rc = _load().orc_legendre_adjoint(rings.nrings, *rings._geo(), lmax,
                                       nmaps, _dp(F.view(np.float64)),
                                       _dp(alm.view(np.float64)), nthreads)
     assert rc == 0
@@ -241,7 +269,7 @@ def adjoint(rings: Rings, lmax: int, maps, nthreads: int = 0) -> np.ndarray:
     nmaps = f.shape[0]
     assert f.shape[1] == rings.npix
     alm = np.zeros((nmaps, nalm(lmax)), dtype=np.complex128)
-    rc = _load().orc_adjoint(rings.nrings, _dp(rings.z), _dp(rings.sinth), _ip(rings.J),
+    rc = _load().orc_adjoint(rings.nrings, *rings._geo(), _ip(rings.J),
                              _ip(rings.s), lmax, nmaps, _dp(f),
                              _dp(alm.view(np.float64)), nthreads)
     assert rc == 0
@@ -255,5 +283,4 @@ def gauss_legendre_rings(nrings: int, nphi: int) -> tuple[Rings, np.ndarray]:
     x, w = np.polynomial.legendre.leggauss(nrings)
     z = x[::-1].copy()
     w = w[::-1].copy()
-    st = np.sqrt((1.0 - z) * (1.0 + z))
-    return Rings(z, st, np.full(nrings, nphi, np.int32), np.zeros(nrings, np.int32)), w
+    return Rings(z, None, np.full(nrings, nphi, np.int32), np.zeros(nrings, np.int32)), w

@@ -33,8 +33,9 @@
  *     2 pi n / (2 J_k) with n = m (2j + s_k) mod 2 J_k.
  *
  * Ring grid description shared by every routine: nrings rings, ring k has
- * z[k] = cos(theta_k), sinth[k] = sin(theta_k) (passed separately so the
- * caller can give it exactly), J[k] pixels and a half-pixel shift flag
+ * z = cos(theta_k) and sin(theta_k), each as a double-double pair
+ * (z[k] + zlo[k], sinth[k] + sinlo[k]) so that the ring position is known to
+ * far better than a double, J[k] pixels and a half-pixel shift flag
  * s[k] in {0,1}: phi_kj = pi (2 j + s_k) / J_k, j = 0..J_k-1.  Pixel values
  * of ring k are stored contiguously, rings in the given order.
  *
@@ -137,15 +138,17 @@ static long long alm_index(int lmax, int l, int m)
  *                                  phi = pi(2j+s)/(4N), s = 1 iff (i+N) even
  *   south ring 4N-i              : mirror of ring i (z -> -z, same J and phi)
  * Pixels are numbered ring by ring from the north pole.
- * z and sin(theta) are each formed from exact integers with one division
- * (and one square root):
+ * z and sin(theta) are returned as double-double pairs (hi, lo), formed
+ * from exact integer ratios:
  *   polar: z = (3N^2 - i^2)/(3N^2),  sin^2 = i^2 (6N^2 - i^2) / (9N^4)
  *   belt : z = (4N - 2i)/(3N),       sin^2 = (2i - N)(7N - 2i) / (9N^2)
+ * (a rounded double z alone moves theta by ~1e-10 relative on the first
+ * ring at Nside = 2048, where 1 - z ~ 8e-8).
  */
 int orc_healpix_nrings(int nside) { return 4 * nside - 1; }
 
-int orc_healpix_rings(int nside, double *z, double *sinth, int *J, int *s,
-                      long long *start)
+int orc_healpix_rings(int nside, double *z, double *zlo, double *sinth,
+                      double *sinlo, int *J, int *s, long long *start)
 {
     if (nside < 1) return -1;
     const long long N = nside;
@@ -153,28 +156,44 @@ int orc_healpix_rings(int nside, double *z, double *sinth, int *J, int *s,
     long long pix = 0;
     for (int r = 1; r <= nr; ++r) {
         const long long i = r <= 2 * nside ? r : 4 * nside - r;
-        double zi, s2;
+        long long zn, zd, sn, sd;     /* z = zn/zd, sin^2 = sn/sd, exact integers */
         int Ji, si;
         if (i < N) {
-            zi = (double)(3 * N * N - i * i) / (double)(3 * N * N);
-            s2 = (double)(i * i * (6 * N * N - i * i)) / (double)(9 * N * N * N * N);
+            zn = 3 * N * N - i * i;  zd = 3 * N * N;
+            sn = i * i * (6 * N * N - i * i);  sd = 9 * N * N * N * N;
             Ji = (int)(4 * i);
             si = 1;
         } else {
-            zi = (double)(4 * N - 2 * i) / (double)(3 * N);
-            s2 = (double)((2 * i - N) * (7 * N - 2 * i)) / (double)(9 * N * N);
+            zn = 4 * N - 2 * i;  zd = 3 * N;
+            sn = (2 * i - N) * (7 * N - 2 * i);  sd = 9 * N * N;
             Ji = (int)(4 * N);
             si = ((i + N) % 2 == 0) ? 1 : 0;
         }
+        dd zz = dd_div(dd_from((double)zn), dd_from((double)zd));
+        dd ss = dd_sqrt(dd_div(dd_from((double)sn), dd_from((double)sd)));
         const int k = r - 1;
-        z[k] = r > 2 * nside ? -zi : zi;
-        sinth[k] = sqrt(s2);
+        if (r > 2 * nside) zz = dd_neg(zz);
+        z[k] = zz.hi;
+        zlo[k] = zz.lo;
+        sinth[k] = ss.hi;
+        sinlo[k] = ss.lo;
         J[k] = Ji;
         s[k] = si;
         if (start) start[k] = pix;
         pix += Ji;
     }
     return 0;
+}
+
+/* sin(theta) = sqrt((1-z)(1+z)) in double-double for rings given by a double z */
+void orc_sin_from_cos(int n, const double *z, double *sinth, double *sinlo)
+{
+    for (int k = 0; k < n; ++k) {
+        dd a = two_sum(1.0, -z[k]), b = two_sum(1.0, z[k]);
+        dd ss = dd_sqrt(dd_mul(a, b));
+        sinth[k] = ss.hi;
+        sinlo[k] = ss.lo;
+    }
 }
 
 /* --------------------------------------------------- Legendre functions */
@@ -236,11 +255,11 @@ static dd dd_normalise(dd x, int *E)
 }
 
 /* s^m as (mantissa, exponent) by binary powering */
-static dd dd_pow_scaled(double s, int m, int *E)
+static dd dd_pow_scaled(dd s, int m, int *E)
 {
     dd r = dd_from(1.0);
     int Er = 0, Eb = 0;
-    dd b = dd_normalise(dd_from(s), &Eb);
+    dd b = dd_normalise(s, &Eb);
     while (m > 0) {
         if (m & 1) {
             r = dd_mul(r, b);
@@ -259,7 +278,7 @@ static dd dd_pow_scaled(double s, int m, int *E)
 }
 
 /* Values at one point for l = m..lmax, as double-double (hi, lo arrays). */
-static void plm_eval(const plm_table *t, double z, double sinth, double *ohi, double *olo)
+static void plm_eval(const plm_table *t, dd z, dd sinth, double *ohi, double *olo)
 {
     const int m = t->m, lmax = t->lmax;
     int E;
@@ -273,10 +292,10 @@ static void plm_eval(const plm_table *t, double z, double sinth, double *ohi, do
     } while (0)
     EMIT(0, p0);
     if (m == lmax) return;
-    dd p1 = dd_mul_d(dd_mul(t->sq, p0), z);
+    dd p1 = dd_mul(dd_mul(t->sq, p0), z);
     EMIT(1, p1);
     for (int l = m + 2; l <= lmax; ++l) {
-        dd a = dd_mul_d(p1, z);
+        dd a = dd_mul(p1, z);
         dd c = dd_mul(t->b[l - 1 - m], p0);
         dd p2 = dd_mul(dd_sub(a, c), t->ib[l - m]);
         p0 = p1;
@@ -300,13 +319,15 @@ static void plm_eval(const plm_table *t, double z, double sinth, double *ohi, do
 #undef EMIT
 }
 
-void orc_legendre(int m, int lmax, double z, double sinth, double *out)
+void orc_legendre(int m, int lmax, double z, double zlo, double sinth,
+                  double sinlo, double *out)
 {
     if (m < 0 || m > lmax) return;
     plm_table t;
     plm_table_init(&t, m, lmax);
     double *lo = (double *)malloc(sizeof(double) * (size_t)(lmax - m + 1));
-    plm_eval(&t, z, sinth, out, lo);
+    const dd zz = {z, zlo}, ss = {sinth, sinlo};
+    plm_eval(&t, zz, ss, out, lo);
     for (int i = 0; i <= lmax - m; ++i) out[i] += lo[i];
     free(lo);
     plm_table_free(&t);
@@ -318,7 +339,8 @@ void orc_legendre(int m, int lmax, double z, double sinth, double *out)
  * for m = 0..lmax at each of the given rings (Eq. legendre-transform).
  * Parallel over m; the sum over l is accumulated in double-double.
  */
-int orc_legendre_q(int nrings, const double *z, const double *sinth, int lmax,
+int orc_legendre_q(int nrings, const double *z, const double *zlo,
+                   const double *sinth, const double *sinlo, int lmax,
                    int nmaps, const double *alm, double *q, int nthreads)
 {
     if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
@@ -337,7 +359,8 @@ int orc_legendre_q(int nrings, const double *z, const double *sinth, int lmax,
             plm_table t;
             plm_table_init(&t, m, lmax);
             for (int k = 0; k < nrings; ++k) {
-                plm_eval(&t, z[k], sinth[k], ph, pl);
+                const dd zk = {z[k], zlo[k]}, sk = {sinth[k], sinlo[k]};
+                plm_eval(&t, zk, sk, ph, pl);
                 for (int b = 0; b < nmaps; ++b) {
                     const double *a = alm + 2 * (size_t)nalm * b;
                     dd re = dd_from(0.0), im = dd_from(0.0);
@@ -425,14 +448,14 @@ int orc_phi_synth(int nrings, const int *J, const int *s, int lmax, int nmaps,
 }
 
 /* Full synthesis: Legendre stage then Fourier stage. */
-int orc_synth(int nrings, const double *z, const double *sinth, const int *J,
-              const int *s, int lmax, int nmaps, const double *alm, double *map,
-              int nthreads)
+int orc_synth(int nrings, const double *z, const double *zlo, const double *sinth,
+              const double *sinlo, const int *J, const int *s, int lmax, int nmaps,
+              const double *alm, double *map, int nthreads)
 {
     size_t nq = 2 * (size_t)nmaps * nrings * (lmax + 1);
     double *q = (double *)malloc(sizeof(double) * (nq ? nq : 1));
     if (!q) return -2;
-    int rc = orc_legendre_q(nrings, z, sinth, lmax, nmaps, alm, q, nthreads);
+    int rc = orc_legendre_q(nrings, z, zlo, sinth, sinlo, lmax, nmaps, alm, q, nthreads);
     if (rc == 0) rc = orc_phi_synth(nrings, J, s, lmax, nmaps, q, map, nthreads);
     free(q);
     return rc;
@@ -494,7 +517,8 @@ int orc_phi_adjoint(int nrings, const int *J, const int *s, int lmax, int nmaps,
  *   (Y^T f)_lm = 2 sum_p f_p Ptilde_l^m(z_p) e^{-i m phi_p}   (m >= 1);
  * it is the Y^dagger of Eq. (wiener) up to the factor 2 for m >= 1.
  */
-int orc_legendre_adjoint(int nrings, const double *z, const double *sinth,
+int orc_legendre_adjoint(int nrings, const double *z, const double *zlo,
+                         const double *sinth, const double *sinlo,
                          int lmax, int nmaps, const double *F, double *alm,
                          int nthreads)
 {
@@ -517,7 +541,8 @@ int orc_legendre_adjoint(int nrings, const double *z, const double *sinth,
             plm_table t;
             plm_table_init(&t, m, lmax);
             for (int k = 0; k < nrings; ++k) {
-                plm_eval(&t, z[k], sinth[k], ph, pl);
+                const dd zk = {z[k], zlo[k]}, sk = {sinth[k], sinlo[k]};
+                plm_eval(&t, zk, sk, ph, pl);
                 for (int b = 0; b < nmaps; ++b) {
                     const double *Fk = F + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
                     dd *ab = acc + 2 * (size_t)n * b;
@@ -548,15 +573,16 @@ int orc_legendre_adjoint(int nrings, const double *z, const double *sinth,
 }
 
 /* Full adjoint: Fourier-stage adjoint then Legendre-stage adjoint. */
-int orc_adjoint(int nrings, const double *z, const double *sinth, const int *J,
-                const int *s, int lmax, int nmaps, const double *map,
-                double *alm, int nthreads)
+int orc_adjoint(int nrings, const double *z, const double *zlo, const double *sinth,
+                const double *sinlo, const int *J, const int *s, int lmax, int nmaps,
+                const double *map, double *alm, int nthreads)
 {
     size_t nF = 2 * (size_t)nmaps * nrings * (lmax + 1);
     double *F = (double *)malloc(sizeof(double) * (nF ? nF : 1));
     if (!F) return -2;
     int rc = orc_phi_adjoint(nrings, J, s, lmax, nmaps, map, F, nthreads);
-    if (rc == 0) rc = orc_legendre_adjoint(nrings, z, sinth, lmax, nmaps, F, alm, nthreads);
+    if (rc == 0)
+        rc = orc_legendre_adjoint(nrings, z, zlo, sinth, sinlo, lmax, nmaps, F, alm, nthreads);
     free(F);
     return rc;
 }

@@ -84,8 +84,12 @@ def test_healpix_rings_match_pixel_formulas(nside):
         zp, php = _healpix_pix2ang(nside, p)
         assert z[p] == pytest.approx(zp, abs=1e-15)
         assert phi[p] == pytest.approx(php, abs=1e-13)
-    # sin(theta) is given exactly, consistent with z
-    np.testing.assert_allclose(rings.sinth ** 2 + rings.z ** 2, 1.0, atol=1e-15)
+    # (z, sin theta) as double-double pairs lie on the unit circle
+    zz = rings.z.astype(np.longdouble) + rings.zlo
+    ss = rings.sinth.astype(np.longdouble) + rings.sinlo
+    assert np.abs(zz * zz + ss * ss - 1).max() < 4 * np.finfo(np.longdouble).eps
+    # and the low parts only refine the doubles
+    assert np.all(np.abs(rings.zlo) <= np.spacing(np.abs(rings.z)))
     # rings are symmetric about the equator
     np.testing.assert_array_equal(rings.J, rings.J[::-1])
     np.testing.assert_allclose(rings.z, -rings.z[::-1], atol=0)
@@ -109,7 +113,7 @@ def test_legendre_closed_forms():
         s = math.sqrt((1 - z) * (1 + z))
         for l, m, sign, C, poly in forms:
             want = sign * math.sqrt(C / math.pi) * eval(poly, {"z": z, "s": s})
-            got = oracle.legendre(m, 3, z, s)[l - m]
+            got = oracle.legendre(m, 3, z)[l - m]
             assert got == pytest.approx(want, rel=1e-14, abs=1e-15), (l, m, z)
 
 
@@ -135,7 +139,7 @@ def test_legendre_diagonal_log_closed_form():
     for k in [0, 1, 5, 40, 300, 2047]:
         z, st = rings.z[k], rings.sinth[k]
         for m in [1, 10, 100, 700, 1500, 4000]:
-            v = oracle.legendre(m, m, z, st)[0]
+            v = oracle.legendre(m, m, z, st, rings.zlo[k], rings.sinlo[k])[0]
             logv = 0.5 * (math.log((2 * m + 1) / (4 * math.pi)) + math.lgamma(2 * m + 1)
                           - 2 * math.lgamma(m + 1) - m * math.log(4)) + m * math.log(st)
             if logv < math.log(1e-290):
@@ -151,23 +155,19 @@ def test_addition_theorem(lmax):
     near-pole, mid and equatorial z (including the first HEALPix ring at
     Nside=2048, where most of the terms underflow).
 
-    A pair of doubles (z, sin theta) is never exactly on the unit circle: a
-    relative mismatch d <= 2^-53 in sin(theta) moves Ptilde_l^m by m*d, so
-    the identity can only hold to about 2*L*2^-53 where large m contribute
-    (mid latitudes).  Near the poles (only small m contribute) and on the
-    equator (z = 0, sin = 1 exactly) it must hold to a few ulp: a plain FP64
-    one-step recurrence misses it by 1.5e-11 at l = 4096 next to the pole."""
+    sin(theta) is formed from z in double-double, so (z, sin theta) lies on
+    the unit circle to ~1e-32 and the identity must hold to a few ulp of the
+    final double sums everywhere (a plain FP64 one-step recurrence misses it
+    by 1.5e-11 at l = 4096 next to the pole and by 2.6e-13 at z = 0.5)."""
     cases = [(1 - 1 / (3 * 2048 ** 2), 1e-14), (1 - 1 / (3 * 64 ** 2), 1e-14), (0.0, 1e-14),
              (0.93, None), (0.5, None), (0.1, None), (-0.77, None)]
     for z, tol in cases:
-        st = math.sqrt((1 - z) * (1 + z))
         acc = np.zeros(lmax + 1)
         for m in range(lmax + 1):
-            p = oracle.legendre(m, lmax, z, st)
+            p = oracle.legendre(m, lmax, z)
             acc[m:] += (1.0 if m == 0 else 2.0) * p * p
         want = (2 * np.arange(lmax + 1) + 1) / (4 * math.pi)
-        rtol = tol if tol is not None else 2.5 * lmax * 2.0 ** -53 + 1e-14
-        np.testing.assert_allclose(acc, want, rtol=rtol)
+        np.testing.assert_allclose(acc, want, rtol=tol if tol is not None else 2e-14)
 
 
 def test_legendre_satisfies_paper_jump_two_recurrence():
