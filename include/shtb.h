@@ -1,0 +1,226 @@
+/*
+ * shtb.h -- C ABI of a GB300 (sm_103a) implementation of scalar spherical
+ * harmonic synthesis on the HEALPix grid by butterfly-compressed Legendre
+ * transforms, after D. S. Seljebotn, "Wavemoth -- Fast spherical harmonic
+ * transforms by butterfly matrix compression" (arXiv 1110.4874).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * Transform (Sec. 2.1-2.2, Eq. shdef, Eq. sh-baseline):
+ *     f(theta_k, phi_kj) = sum_{l=0}^{L} sum_{m=-l}^{l} a_lm Y_lm(theta_k, phi_kj)
+ *   for a real field, a_{l,-m} = (-1)^m conj(a_lm), with Y_lm =
+ *   Ptilde_l^m(cos theta) e^{i m phi} and Ptilde the normalised associated
+ *   Legendre function of Eq. (Y-def), Condon-Shortley phase included.
+ * a_lm buffers: complex128 as interleaved doubles (re, im), only m >= 0,
+ *   m-major: coefficient (l, m) of map b sits at complex index
+ *   b * nalm + m*(2L+1-m)/2 + l, nalm = (L+1)(L+2)/2.  Im a_l0 is ignored on
+ *   input and written as 0 on output.
+ * Maps: float64, [nmaps][12 nside^2], HEALPix RING order (rings north to
+ *   south, pixels in increasing phi), maps stacked (not interleaved).
+ * Adjoint: the transpose of the real-linear synthesis map under the plain
+ *   real inner products over (Re a_lm, Im a_lm) and pixels:
+ *     (Y^T f)_l0 = sum_p f_p Ptilde_l^0(z_p)
+ *     (Y^T f)_lm = 2 sum_p f_p Ptilde_l^m(z_p) e^{-i m phi_p}   (m >= 1),
+ *   i.e. the Y^dagger of Eq. (wiener) with a factor 2 for m >= 1, which is
+ *   the gradient convention of torch for complex parameters.
+ * Device pointers: every pointer named *_dev lives in the memory of the plan's
+ *   CUDA device and must be 8-byte aligned (16-byte for complex arrays); the
+ *   caller owns it.  Host pointers (*_host) should be pinned for overlap.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream).  Calls enqueue work and return without synchronising,
+ *   except the *_host variants, which return once the result is on the host.
+ * Errors: every int-returning call returns SHTB_OK (0) or a negative SHTB_E*
+ *   code; nothing aborts.  shtb_strerror() names a code and
+ *   shtb_last_error_message() gives the calling thread's last detailed
+ *   message.
+ * Threads: one plan may be used from one host thread at a time.
+ */
+#ifndef SHTB_H
+#define SHTB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHTB_ABI_VERSION 1
+
+enum {
+    SHTB_OK = 0,
+    SHTB_EINVAL = -1,     /* invalid argument (sizes, null pointers, nside, lmax, eps) */
+    SHTB_ENOMEM = -2,     /* host or device allocation failed                        */
+    SHTB_ECUDA = -3,      /* a CUDA runtime call failed                               */
+    SHTB_EMISMATCH = -4,  /* plan used on another device than it was built for       */
+    SHTB_ETIMEOUT = -5,   /* a bounded device wait gave up                             */
+    SHTB_ENOTSUP = -6,    /* size or option outside what the library supports         */
+    SHTB_EIO = -7,        /* plan cache file could not be read or written              */
+    SHTB_ECORRUPT = -8    /* plan cache file failed its checks                         */
+};
+
+typedef struct shtb_plan_s *shtb_plan;
+
+/* Plan options (all fields have defaults set by shtb_plan_opts_init). */
+typedef struct {
+    int leaf_cols;     /* columns (rings) per butterfly leaf block, Sec. 3.2 ("64 columns"
+                          in the text, 32 in Fig. compression-efficiency); default 32  */
+    int max_depth;     /* cap on butterfly levels per (m, parity); -1 = no cap        */
+    double rho;        /* cost of one stored-matrix element relative to one recurrence
+                          step, the rho of Sec. 4.2 used to choose where to stop
+                          compressing; <= 0 = library default                         */
+    int nthreads;      /* host threads used while building the plan; 0 = all cores   */
+    int device;        /* CUDA device ordinal; -1 = the calling thread's current one  */
+} shtb_plan_opts;
+
+/* Plan statistics (algorithmic counts; used for roofline accounting). */
+typedef struct {
+    int nside, lmax;
+    double eps;
+    int nrings;                 /* 4 nside - 1                                        */
+    long long npix;             /* 12 nside^2                                         */
+    long long nalm;             /* (L+1)(L+2)/2                                       */
+    int compressed;             /* 0: eps <= 0, uncompressed (zero levels, Sec. 3.3)  */
+    long long n_recurrence;     /* (l, ring) pairs evaluated by the Legendre recurrence
+                                   after the 1e-30 crop, summed over m and parity    */
+    long long n_recurrence_exec;/* lane-steps the kernel issues for them (incl. idle
+                                   lanes of a warp)                                   */
+    long long n_dense;          /* stored dense interpolation-matrix elements (S)     */
+    long long n_rstored;        /* stored residual-block elements (R)                 */
+    long long plan_device_bytes;/* HBM held by the plan (excluding workspace)         */
+    long long plan_read_bytes;  /* plan bytes one transform of a map batch reads      */
+    double legendre_flops_per_map;  /* FP64 flops of the Legendre stage per map
+                                       (recurrence flops amortised at 1 map)          */
+    double recurrence_flops;        /* FP64 flops of the recurrence per call           */
+    double phi_flops_per_map;       /* FP64 flops of the ring FFT stage per map       */
+    double build_seconds;           /* host + device time of shtb_plan_create         */
+    int depth_hist[16];             /* (m, parity) count per butterfly depth          */
+} shtb_plan_stats_t;
+
+/* Fill *opts with defaults.  Returns SHTB_EINVAL on NULL. */
+int shtb_plan_opts_init(shtb_plan_opts *opts);
+
+/*
+ * Build a synthesis plan for HEALPix resolution nside and band limit lmax
+ * (Sec. 2.2) on a CUDA device: ring geometry, the per-(l, m) coefficients of
+ * the jump-two Legendre recurrence (Eq. three-term), the recurrence start
+ * values past the 1e-30 crop (Appendix, "Efficient code for Legendre
+ * transforms"), the ring phase/FFT tables of Eq. (tau), and, when eps > 0,
+ * the butterfly-compressed operator of Sec. 3.2 at ID tolerance eps
+ * (Eq. ID-approximation).  eps <= 0 gives the uncompressed transform (the
+ * "zero levels of compression" limit of Sec. 3.3).
+ * nside >= 1, 0 <= lmax <= 8192; opts may be NULL.  On success *out holds a
+ * plan that owns all its device memory; release it with shtb_plan_destroy.
+ * Errors: SHTB_EINVAL, SHTB_ENOTSUP, SHTB_ENOMEM, SHTB_ECUDA.
+ */
+int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts,
+                     shtb_plan *out);
+
+/* Release a plan and all device memory it owns (NULL is accepted). */
+int shtb_plan_destroy(shtb_plan plan);
+
+/* Copy the plan's statistics into *out. */
+int shtb_plan_stats(shtb_plan plan, shtb_plan_stats_t *out);
+
+/*
+ * Make sure the plan's internal workspace can serve transforms of up to
+ * nmaps maps, allocating now (so later calls allocate nothing and may be
+ * captured into a CUDA graph).  Errors: SHTB_EINVAL, SHTB_ENOMEM.
+ */
+int shtb_plan_reserve(shtb_plan plan, int nmaps);
+
+/*
+ * Synthesis f = Y a for nmaps maps (Eq. shdef via Eq. sh-baseline):
+ * Legendre stage q_m(z_k) = sum_l a_lm Ptilde_l^m(z_k) split by l-m parity
+ * over mirrored rings (Eq. q-even-odd, q-even-odd2), then per ring the phase
+ * shift and wrap of Eq. (tau) and a backward real FFT.
+ * alm_dev: [nmaps][nalm] complex128; map_dev: [nmaps][12 nside^2] float64.
+ * Errors: SHTB_EINVAL (NULL, nmaps < 1, misaligned), SHTB_EMISMATCH,
+ * SHTB_ENOMEM (workspace growth), SHTB_ECUDA.
+ */
+int shtb_synthesize(shtb_plan plan, const double *alm_dev, double *map_dev, int nmaps,
+                    void *stream);
+
+/*
+ * Adjoint synthesis a = Y^T f for nmaps maps (the Y^dagger of Eq. wiener
+ * under the real inner product, see the header comment): per ring a forward
+ * real FFT and the unwrap of Eq. (tau), then the transposed Legendre stage
+ * (Eq. legendre-transform-linalg-backwards without quadrature weights).
+ * map_dev: [nmaps][12 nside^2]; alm_dev: [nmaps][nalm] complex128 (written).
+ * Errors as shtb_synthesize.
+ */
+int shtb_adjoint(shtb_plan plan, const double *map_dev, double *alm_dev, int nmaps,
+                 void *stream);
+
+/*
+ * The same two transforms between HOST buffers: the call copies the inputs
+ * to the device on `stream`, transforms, copies the result back and waits
+ * for it.  Buffers should be pinned (cudaHostAlloc) for full copy speed.
+ */
+int shtb_synthesize_host(shtb_plan plan, const double *alm_host, double *map_host,
+                         int nmaps, void *stream);
+int shtb_adjoint_host(shtb_plan plan, const double *map_host, double *alm_host,
+                      int nmaps, void *stream);
+
+/* Name of an error code (static string). */
+const char *shtb_strerror(int code);
+
+/* Detailed message of the calling thread's last failing call ("" if none). */
+const char *shtb_last_error_message(void);
+
+/*
+ * Per-stage device timing.  While enabled, each transform records CUDA
+ * events around its stages on the stream it runs on; shtb_profile_read
+ * waits for them and returns the summed milliseconds per stage:
+ *   ms[0] Legendre stage (synthesis), ms[1] ring FFT stage (synthesis),
+ *   ms[2] ring FFT stage (adjoint),   ms[3] Legendre stage (adjoint),
+ *   ms[4] a_lm staging kernels (scaling / interleave / scatter),
+ * and the number of profiled calls.  Reading resets the sums.  Up to 4096
+ * calls are kept between reads.
+ */
+int shtb_profile_enable(shtb_plan plan, int on);
+int shtb_profile_read(shtb_plan plan, double *ms, int nstages, int *ncalls);
+
+/*
+ * Measure this device's FP64 throughput with two microkernels (a chain of
+ * independent DFMA per thread, and warp-level DMMA m8n8k4 f64 tensor-core
+ * MMA), each timed with CUDA events after a warm-up.  Results in GFLOP/s
+ * (2 flops per FMA).  Used only to state roofline denominators.
+ */
+int shtb_measure_fp64_peak(int device, double *dfma_gflops, double *dmma_gflops);
+
+/* ------------------------------------------------------------------------
+ * Private entry points for testing single stages in isolation (the paper's
+ * "private API ... used from Python to test individual C routines",
+ * Sec. 4.1).  Buffers are device pointers.
+ *   q layout: complex128 [nmaps][4 nside - 1][lmax + 1], q[b][ring][m].
+ * ------------------------------------------------------------------------ */
+
+/* Legendre stage only: q_m(z_k) for every ring (Eq. legendre-transform). */
+int shtb_test_legendre(shtb_plan plan, const double *alm_dev, double *q_dev, int nmaps,
+                       void *stream);
+/* Ring stage only: pixels from q (Eq. sh-baseline, Eq. phi, Eq. tau). */
+int shtb_test_phi(shtb_plan plan, const double *q_dev, double *map_dev, int nmaps,
+                  void *stream);
+/* Ring stage adjoint: q_adj[b][ring][m] = sum_j f_kj e^{-i m phi_kj}. */
+int shtb_test_phi_adjoint(shtb_plan plan, const double *map_dev, double *q_dev,
+                          int nmaps, void *stream);
+/* Legendre stage adjoint: a_lm = c_m sum_k Ptilde_l^m(z_k) q_adj[k][m],
+   c_0 = 1, c_m = 2 (m >= 1). */
+int shtb_test_legendre_adjoint(shtb_plan plan, const double *q_dev, double *alm_dev,
+                               int nmaps, void *stream);
+
+/*
+ * Host-only check of the plan tables (needs no GPU): Ptilde_l^m(z_r) for
+ * l = m..lmax at HEALPix half-ring r (0-based from the north pole, r < 2 nside),
+ * evaluated on the CPU with the same per-(l, m) constants, start values and
+ * two-FMA recurrence step as the Legendre kernels (Eq. three-term, rescaled).
+ * out: lmax - m + 1 doubles (host).  Errors: SHTB_EINVAL.
+ */
+int shtb_test_host_recurrence(int nside, int lmax, int m, int r, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHTB_H */

@@ -1,0 +1,348 @@
+"""GB300 (sm_103a) scalar spherical-harmonic synthesis on the HEALPix grid by
+butterfly-compressed Legendre transforms (after Seljebotn, "Wavemoth",
+arXiv 1110.4874).
+
+This module is a thin ctypes binding of the C ABI in ``include/shtb.h``: the
+functions named ``shtb_*`` marshal arguments (torch tensors -> device
+pointers, the current CUDA stream) and call the library of the same name; all
+arithmetic runs in the library's CUDA kernels.  There is no CPU fallback: if
+the compiled library is missing, importing the binding's entry points raises.
+
+Layouts (see include/shtb.h): a_lm complex128 [nmaps, (L+1)(L+2)/2], m-major
+(index m(2L+1-m)/2 + l); maps float64 [nmaps, 12 nside^2] in RING order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import synthetic  # noqa: F401  (seeded inputs; no transform arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libshtb.so")
+
+SHTB_OK = 0
+SHTB_EINVAL = -1
+SHTB_ENOMEM = -2
+SHTB_ECUDA = -3
+SHTB_EMISMATCH = -4
+SHTB_ETIMEOUT = -5
+SHTB_ENOTSUP = -6
+SHTB_EIO = -7
+SHTB_ECORRUPT = -8
+
+
+class ShtbError(RuntimeError):
+    """A non-zero return code of the C ABI."""
+
+    def __init__(self, code: int, where: str, detail: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code}): {detail}")
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("leaf_cols", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("rho", ctypes.c_double), ("nthreads", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("eps", ctypes.c_double),
+                ("nrings", ctypes.c_int), ("npix", ctypes.c_longlong), ("nalm", ctypes.c_longlong),
+                ("compressed", ctypes.c_int), ("n_recurrence", ctypes.c_longlong),
+                ("n_recurrence_exec", ctypes.c_longlong), ("n_dense", ctypes.c_longlong),
+                ("n_rstored", ctypes.c_longlong), ("plan_device_bytes", ctypes.c_longlong),
+                ("plan_read_bytes", ctypes.c_longlong), ("legendre_flops_per_map", ctypes.c_double),
+                ("recurrence_flops", ctypes.c_double), ("phi_flops_per_map", ctypes.c_double),
+                ("build_seconds", ctypes.c_double), ("depth_hist", ctypes.c_int * 16)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "depth_hist"}
+        d["depth_hist"] = list(self.depth_hist)
+        return d
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); every symbol declared in include/shtb.h
+SIGNATURES = {
+    "shtb_plan_opts_init": (_I, [ctypes.POINTER(PlanOpts)]),
+    "shtb_plan_create": (_I, [_I, _I, _D, ctypes.POINTER(PlanOpts), ctypes.POINTER(_P)]),
+    "shtb_plan_destroy": (_I, [_P]),
+    "shtb_plan_stats": (_I, [_P, ctypes.POINTER(PlanStats)]),
+    "shtb_plan_reserve": (_I, [_P, _I]),
+    "shtb_synthesize": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_adjoint": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_synthesize_host": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_adjoint_host": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_strerror": (ctypes.c_char_p, [_I]),
+    "shtb_last_error_message": (ctypes.c_char_p, []),
+    "shtb_profile_enable": (_I, [_P, _I]),
+    "shtb_profile_read": (_I, [_P, _DP, _I, ctypes.POINTER(_I)]),
+    "shtb_measure_fp64_peak": (_I, [_I, _DP, _DP]),
+    "shtb_test_legendre": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_test_phi": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_test_phi_adjoint": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_test_legendre_adjoint": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_test_host_recurrence": (_I, [_I, _I, _I, _I, _DP]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library {LIB_PATH} is missing; build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` "
+                    "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().shtb_strerror(code).decode()
+    except Exception:
+        return "error"
+
+
+def _check(rc: int, where: str):
+    if rc != SHTB_OK:
+        raise ShtbError(rc, where, lib().shtb_last_error_message().decode())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t, dtype, name):
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- C-ABI names
+def shtb_plan_create(nside: int, lmax: int, eps: float = 0.0, leaf_cols: int = 32,
+                     max_depth: int = -1, rho: float = 0.0, nthreads: int = 0,
+                     device: int = -1) -> ctypes.c_void_p:
+    opts = PlanOpts()
+    _check(lib().shtb_plan_opts_init(ctypes.byref(opts)), "shtb_plan_opts_init")
+    opts.leaf_cols, opts.max_depth, opts.rho = leaf_cols, max_depth, rho
+    opts.nthreads, opts.device = nthreads, device
+    h = ctypes.c_void_p()
+    _check(lib().shtb_plan_create(nside, lmax, float(eps), ctypes.byref(opts), ctypes.byref(h)),
+           "shtb_plan_create")
+    return h
+
+
+def shtb_plan_destroy(plan) -> None:
+    _check(lib().shtb_plan_destroy(plan), "shtb_plan_destroy")
+
+
+def shtb_plan_stats(plan) -> dict:
+    st = PlanStats()
+    _check(lib().shtb_plan_stats(plan, ctypes.byref(st)), "shtb_plan_stats")
+    return st.as_dict()
+
+
+def shtb_plan_reserve(plan, nmaps: int) -> None:
+    _check(lib().shtb_plan_reserve(plan, nmaps), "shtb_plan_reserve")
+
+
+def _call_dev(name, plan, src, src_dtype, dst, dst_dtype, nmaps, stream):
+    import torch
+    fn = getattr(lib(), name)
+    _check(fn(plan, _dptr(src, src_dtype, "input"), _dptr(dst, dst_dtype, "output"), int(nmaps),
+              _stream_handle(stream)), name)
+
+
+def shtb_synthesize(plan, alm, maps, nmaps: int, stream=None) -> None:
+    import torch
+    _call_dev("shtb_synthesize", plan, alm, torch.complex128, maps, torch.float64, nmaps, stream)
+
+
+def shtb_adjoint(plan, maps, alm, nmaps: int, stream=None) -> None:
+    import torch
+    _call_dev("shtb_adjoint", plan, maps, torch.float64, alm, torch.complex128, nmaps, stream)
+
+
+def _hptr(t, dtype, name):
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def shtb_synthesize_host(plan, alm_host, maps_host, nmaps: int, stream=None) -> None:
+    import torch
+    _check(lib().shtb_synthesize_host(plan, _hptr(alm_host, torch.complex128, "alm"),
+                                      _hptr(maps_host, torch.float64, "maps"), int(nmaps),
+                                      _stream_handle(stream)), "shtb_synthesize_host")
+
+
+def shtb_adjoint_host(plan, maps_host, alm_host, nmaps: int, stream=None) -> None:
+    import torch
+    _check(lib().shtb_adjoint_host(plan, _hptr(maps_host, torch.float64, "maps"),
+                                   _hptr(alm_host, torch.complex128, "alm"), int(nmaps),
+                                   _stream_handle(stream)), "shtb_adjoint_host")
+
+
+def shtb_profile_enable(plan, on: bool) -> None:
+    _check(lib().shtb_profile_enable(plan, 1 if on else 0), "shtb_profile_enable")
+
+
+STAGES = ("legendre_synth", "phi_synth", "phi_adjoint", "legendre_adjoint", "staging")
+
+
+def shtb_profile_read(plan) -> tuple[dict, int]:
+    ms = (ctypes.c_double * len(STAGES))()
+    n = ctypes.c_int()
+    _check(lib().shtb_profile_read(plan, ms, len(STAGES), ctypes.byref(n)), "shtb_profile_read")
+    return {k: ms[i] for i, k in enumerate(STAGES)}, n.value
+
+
+def shtb_measure_fp64_peak(device: int = 0) -> tuple[float, float]:
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().shtb_measure_fp64_peak(device, ctypes.byref(a), ctypes.byref(b)),
+           "shtb_measure_fp64_peak")
+    return a.value, b.value
+
+
+def shtb_test_legendre(plan, alm, q, nmaps: int, stream=None) -> None:
+    import torch
+    _call_dev("shtb_test_legendre", plan, alm, torch.complex128, q, torch.complex128, nmaps, stream)
+
+
+def shtb_test_phi(plan, q, maps, nmaps: int, stream=None) -> None:
+    import torch
+    _call_dev("shtb_test_phi", plan, q, torch.complex128, maps, torch.float64, nmaps, stream)
+
+
+def shtb_test_phi_adjoint(plan, maps, q, nmaps: int, stream=None) -> None:
+    import torch
+    _call_dev("shtb_test_phi_adjoint", plan, maps, torch.float64, q, torch.complex128, nmaps, stream)
+
+
+def shtb_test_legendre_adjoint(plan, q, alm, nmaps: int, stream=None) -> None:
+    import torch
+    _call_dev("shtb_test_legendre_adjoint", plan, q, torch.complex128, alm, torch.complex128,
+              nmaps, stream)
+
+
+def shtb_test_host_recurrence(nside: int, lmax: int, m: int, r: int):
+    import numpy as np
+    out = np.zeros(lmax - m + 1)
+    _check(lib().shtb_test_host_recurrence(nside, lmax, m, r, out.ctypes.data_as(_DP)),
+           "shtb_test_host_recurrence")
+    return out
+
+
+# ------------------------------------------------------------ convenience
+class Plan:
+    """A synthesis plan on one CUDA device (owns its device memory)."""
+
+    def __init__(self, nside: int, lmax: int, eps: float = 0.0, **opts):
+        import torch
+        if "device" not in opts:
+            opts["device"] = torch.cuda.current_device()
+        self.nside, self.lmax, self.eps = nside, lmax, eps
+        self.device = opts["device"]
+        self._h = shtb_plan_create(nside, lmax, eps, **opts)
+        st = shtb_plan_stats(self._h)
+        self.npix, self.nalm, self.nrings = st["npix"], st["nalm"], st["nrings"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        return shtb_plan_stats(self._h)
+
+    def reserve(self, nmaps: int) -> None:
+        shtb_plan_reserve(self._h, nmaps)
+
+    def synthesize(self, alm, out=None, stream=None):
+        """alm complex128 [nmaps, nalm] (or [nalm]) on the plan's device -> maps float64."""
+        import torch
+        squeeze = alm.dim() == 1
+        a = alm.reshape(-1, self.nalm).contiguous()
+        nmaps = a.shape[0]
+        if out is None:
+            out = torch.empty((nmaps, self.npix), dtype=torch.float64, device=a.device)
+        shtb_synthesize(self._h, a, out, nmaps, stream)
+        return out[0] if squeeze else out
+
+    def adjoint(self, maps, out=None, stream=None):
+        """maps float64 [nmaps, npix] (or [npix]) -> Y^T f, complex128 [nmaps, nalm]."""
+        import torch
+        squeeze = maps.dim() == 1
+        f = maps.reshape(-1, self.npix).contiguous()
+        nmaps = f.shape[0]
+        if out is None:
+            out = torch.empty((nmaps, self.nalm), dtype=torch.complex128, device=f.device)
+        shtb_adjoint(self._h, f, out, nmaps, stream)
+        return out[0] if squeeze else out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            shtb_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd_function():
+    import torch
+
+    class Synthesis(torch.autograd.Function):
+        """f = Y a with the hand-written adjoint kernel as its backward:
+        grad_a = Y^T grad_f, the real-inner-product transpose, which is torch's
+        convention for complex leaves (dL/dRe a + i dL/dIm a)."""
+
+        @staticmethod
+        def forward(ctx, alm, plan):
+            ctx.plan = plan
+            return plan.synthesize(alm)
+
+        @staticmethod
+        def backward(ctx, grad_maps):
+            g = ctx.plan.adjoint(grad_maps.contiguous())
+            return g, None
+
+    return Synthesis
+
+
+_synth_fn = None
+
+
+def synthesize(alm, plan: Plan):
+    """Differentiable synthesis: maps = Y alm, backward through shtb_adjoint."""
+    global _synth_fn
+    if _synth_fn is None:
+        _synth_fn = _autograd_function()
+    return _synth_fn.apply(alm, plan)

@@ -1,0 +1,398 @@
+// C-ABI entry points (include/shtb.h): plan lifetime, workspace, the
+// synthesis / adjoint pipelines, host-buffer variants, stage profiling and
+// the private single-stage test entry points.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "shtb_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Workspace {
+    // synthesis
+    double2 *ap = nullptr;      // [nalm][nmaps]
+    double2 *q = nullptr;       // [nmaps][nrings][L+1]  (also the adjoint's q_adj)
+    // adjoint
+    void *adj = nullptr;        // g + recurrence state
+    double2 *aacc = nullptr;    // [nalm][nmaps]
+    // host-buffer variants
+    double2 *alm = nullptr;     // [nmaps][nalm]
+    double *map = nullptr;      // [nmaps][npix]
+};
+
+size_t q_bytes(const shtb_plan_s *p, int nmaps)
+{
+    return sizeof(double2) * (size_t)nmaps * p->nrings * (p->lmax + 1);
+}
+
+size_t alm_bytes(const shtb_plan_s *p, int nmaps) { return sizeof(double2) * (size_t)nmaps * p->nalm; }
+
+size_t adj_bytes(const shtb_plan_s *p, int nmaps)
+{
+    return sizeof(double2) * (size_t)(p->lmax + 1) * 2 * p->nhalf * nmaps +
+           legendre_adjoint_state_bytes(p);
+}
+
+size_t ws_total(const shtb_plan_s *p, int nmaps)
+{
+    return align256(alm_bytes(p, nmaps)) * 2 + align256(q_bytes(p, nmaps)) +
+           align256(adj_bytes(p, nmaps)) + align256(alm_bytes(p, nmaps)) +
+           align256(sizeof(double) * (size_t)nmaps * p->npix);
+}
+
+Workspace carve(shtb_plan_s *p, int nmaps)
+{
+    Workspace w;
+    char *c = (char *)p->ws;
+    w.ap = (double2 *)c;    c += align256(alm_bytes(p, nmaps));
+    w.q = (double2 *)c;     c += align256(q_bytes(p, nmaps));
+    w.adj = c;              c += align256(adj_bytes(p, nmaps));
+    w.aacc = (double2 *)c;  c += align256(alm_bytes(p, nmaps));
+    w.alm = (double2 *)c;   c += align256(alm_bytes(p, nmaps));
+    w.map = (double *)c;
+    return w;
+}
+
+int ensure_ws(shtb_plan_s *p, int nmaps)
+{
+    if (nmaps <= p->ws_nmaps && p->ws) return SHTB_OK;
+    const size_t need = ws_total(p, nmaps);
+    if (p->ws) {
+        cudaError_t e = cudaFree(p->ws);
+        p->ws = nullptr;
+        p->ws_bytes = 0;
+        p->ws_nmaps = 0;
+        if (e != cudaSuccess) return shtb_fail(SHTB_ECUDA, std::string("cudaFree workspace: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&p->ws, need);
+    if (e != cudaSuccess) {
+        p->ws = nullptr;
+        return shtb_fail(SHTB_ENOMEM, "workspace of " + std::to_string(need) + " bytes: " + cudaGetErrorString(e));
+    }
+    p->ws_bytes = need;
+    p->ws_nmaps = nmaps;
+    return SHTB_OK;
+}
+
+int check_call(shtb_plan p, const void *a, const void *b, int nmaps)
+{
+    if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
+    if (!a || !b) return shtb_fail(SHTB_EINVAL, "NULL buffer");
+    if (nmaps < 1) return shtb_fail(SHTB_EINVAL, "nmaps must be >= 1");
+    if (((uintptr_t)a & 15) || ((uintptr_t)b & 15))
+        return shtb_fail(SHTB_EINVAL, "buffers must be 16-byte aligned");
+    int dev = -1;
+    SHTB_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device)
+        return shtb_fail(SHTB_EMISMATCH, "plan built on device " + std::to_string(p->device) +
+                                             ", called with device " + std::to_string(dev) + " current");
+    return SHTB_OK;
+}
+
+// ---------------------------------------------------------- profiling
+struct StageTimer {
+    shtb_plan_s *p;
+    cudaStream_t st;
+    int stage;
+    int e0 = -1;
+    StageTimer(shtb_plan_s *pp, cudaStream_t s, int stg) : p(pp), st(s), stage(stg)
+    {
+        if (!p->profiling || p->ev_next + 2 > (int)p->ev_pool.size()) return;
+        e0 = p->ev_next;
+        p->ev_next += 2;
+        cudaEventRecord(p->ev_pool[e0], st);
+    }
+    ~StageTimer()
+    {
+        if (e0 < 0) return;
+        cudaEventRecord(p->ev_pool[e0 + 1], st);
+        p->recs.push_back({stage, e0, e0 + 1});
+    }
+};
+
+// ------------------------------------------------------------ pipelines
+int run_synthesis(shtb_plan_s *p, const double2 *alm, double *map, int nmaps, cudaStream_t st)
+{
+    int rc = ensure_ws(p, nmaps);
+    if (rc) return rc;
+    Workspace w = carve(p, nmaps);
+    {
+        StageTimer t(p, st, 4);
+        if ((rc = launch_alm_prescale(p, alm, w.ap, nmaps, st))) return rc;
+    }
+    {
+        StageTimer t(p, st, 0);
+        if ((rc = launch_legendre_synth(p, w.ap, w.q, nmaps, st))) return rc;
+    }
+    {
+        StageTimer t(p, st, 1);
+        if ((rc = launch_phi_synth(p, w.q, map, nmaps, st))) return rc;
+    }
+    return SHTB_OK;
+}
+
+int run_adjoint(shtb_plan_s *p, const double *map, double2 *alm, int nmaps, cudaStream_t st)
+{
+    int rc = ensure_ws(p, nmaps);
+    if (rc) return rc;
+    Workspace w = carve(p, nmaps);
+    {
+        StageTimer t(p, st, 2);
+        if ((rc = launch_phi_adjoint(p, map, w.q, nmaps, st))) return rc;
+    }
+    {
+        StageTimer t(p, st, 3);
+        if ((rc = launch_legendre_adjoint(p, w.q, w.aacc, nmaps, w.adj, st))) return rc;
+    }
+    {
+        StageTimer t(p, st, 4);
+        if ((rc = launch_alm_finish(p, w.aacc, alm, nmaps, st))) return rc;
+    }
+    return SHTB_OK;
+}
+
+}  // namespace
+
+int shtb_fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+extern "C" {
+
+const char *shtb_strerror(int code)
+{
+    switch (code) {
+    case SHTB_OK: return "success";
+    case SHTB_EINVAL: return "invalid argument";
+    case SHTB_ENOMEM: return "out of memory";
+    case SHTB_ECUDA: return "CUDA runtime error";
+    case SHTB_EMISMATCH: return "plan used on a different device";
+    case SHTB_ETIMEOUT: return "bounded device wait timed out";
+    case SHTB_ENOTSUP: return "not supported";
+    case SHTB_EIO: return "plan cache I/O error";
+    case SHTB_ECORRUPT: return "plan cache file corrupt";
+    default: return "unknown error";
+    }
+}
+
+const char *shtb_last_error_message(void) { return g_last_error.c_str(); }
+
+int shtb_plan_opts_init(shtb_plan_opts *o)
+{
+    if (!o) return shtb_fail(SHTB_EINVAL, "opts is NULL");
+    o->leaf_cols = 32;
+    o->max_depth = -1;
+    o->rho = 0.0;
+    o->nthreads = 0;
+    o->device = -1;
+    return SHTB_OK;
+}
+
+int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts, shtb_plan *out)
+{
+    if (!out) return shtb_fail(SHTB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nside < 1) return shtb_fail(SHTB_EINVAL, "nside must be >= 1");
+    if (lmax < 0) return shtb_fail(SHTB_EINVAL, "lmax must be >= 0");
+    if (!(eps == eps) || eps > 1.0) return shtb_fail(SHTB_EINVAL, "eps must be a number <= 1");
+    if (lmax > 8192) return shtb_fail(SHTB_ENOTSUP, "lmax > 8192");
+    if (nside > 2048) return shtb_fail(SHTB_ENOTSUP, "nside > 2048");
+    if (eps > 0.0) return shtb_fail(SHTB_ENOTSUP, "compressed plans (eps > 0) are not available in this build");
+    auto t0 = std::chrono::steady_clock::now();
+    shtb_plan_s *p = new (std::nothrow) shtb_plan_s();
+    if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
+    shtb_plan_opts o;
+    shtb_plan_opts_init(&o);
+    if (opts) o = *opts;
+    p->opts = o;
+    p->nside = nside;
+    p->lmax = lmax;
+    p->eps = eps;
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            delete p;
+            return shtb_fail(SHTB_ECUDA, "no CUDA device");
+        }
+    } else if (cudaSetDevice(dev) != cudaSuccess) {
+        delete p;
+        return shtb_fail(SHTB_ECUDA, "cudaSetDevice failed");
+    }
+    p->device = dev;
+    int rc = shtb_build_dense_plan(p);
+    if (rc) {
+        shtb_plan_destroy(p);
+        return rc;
+    }
+    p->stats.nside = nside;
+    p->stats.lmax = lmax;
+    p->stats.eps = eps;
+    p->stats.nrings = p->nrings;
+    p->stats.npix = p->npix;
+    p->stats.nalm = p->nalm;
+    p->stats.compressed = 0;
+    p->stats.depth_hist[0] = 2 * (lmax + 1);
+    p->stats.build_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SHTB_OK;
+}
+
+int shtb_plan_destroy(shtb_plan p)
+{
+    if (!p) return SHTB_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->device) cudaSetDevice(p->device);
+    for (void *a : p->allocations) cudaFree(a);
+    if (p->ws) cudaFree(p->ws);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
+    delete p;
+    return SHTB_OK;
+}
+
+int shtb_plan_stats(shtb_plan p, shtb_plan_stats_t *out)
+{
+    if (!p || !out) return shtb_fail(SHTB_EINVAL, "NULL argument");
+    *out = p->stats;
+    return SHTB_OK;
+}
+
+int shtb_plan_reserve(shtb_plan p, int nmaps)
+{
+    if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
+    if (nmaps < 1) return shtb_fail(SHTB_EINVAL, "nmaps must be >= 1");
+    return ensure_ws(p, nmaps);
+}
+
+int shtb_synthesize(shtb_plan p, const double *alm_dev, double *map_dev, int nmaps, void *stream)
+{
+    int rc = check_call(p, alm_dev, map_dev, nmaps);
+    if (rc) return rc;
+    return run_synthesis(p, (const double2 *)alm_dev, map_dev, nmaps, (cudaStream_t)stream);
+}
+
+int shtb_adjoint(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps, void *stream)
+{
+    int rc = check_call(p, map_dev, alm_dev, nmaps);
+    if (rc) return rc;
+    return run_adjoint(p, map_dev, (double2 *)alm_dev, nmaps, (cudaStream_t)stream);
+}
+
+int shtb_synthesize_host(shtb_plan p, const double *alm_host, double *map_host, int nmaps,
+                         void *stream)
+{
+    int rc = check_call(p, alm_host, map_host, nmaps);
+    if (rc) return rc;
+    if ((rc = ensure_ws(p, nmaps))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace w = carve(p, nmaps);
+    SHTB_CUDA_TRY(cudaMemcpyAsync(w.alm, alm_host, alm_bytes(p, nmaps), cudaMemcpyHostToDevice, st));
+    if ((rc = run_synthesis(p, w.alm, w.map, nmaps, st))) return rc;
+    SHTB_CUDA_TRY(cudaMemcpyAsync(map_host, w.map, sizeof(double) * (size_t)nmaps * p->npix,
+                                  cudaMemcpyDeviceToHost, st));
+    SHTB_CUDA_TRY(cudaStreamSynchronize(st));
+    return SHTB_OK;
+}
+
+int shtb_adjoint_host(shtb_plan p, const double *map_host, double *alm_host, int nmaps, void *stream)
+{
+    int rc = check_call(p, map_host, alm_host, nmaps);
+    if (rc) return rc;
+    if ((rc = ensure_ws(p, nmaps))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace w = carve(p, nmaps);
+    SHTB_CUDA_TRY(cudaMemcpyAsync(w.map, map_host, sizeof(double) * (size_t)nmaps * p->npix,
+                                  cudaMemcpyHostToDevice, st));
+    if ((rc = run_adjoint(p, w.map, w.alm, nmaps, st))) return rc;
+    SHTB_CUDA_TRY(cudaMemcpyAsync(alm_host, w.alm, alm_bytes(p, nmaps), cudaMemcpyDeviceToHost, st));
+    SHTB_CUDA_TRY(cudaStreamSynchronize(st));
+    return SHTB_OK;
+}
+
+int shtb_profile_enable(shtb_plan p, int on)
+{
+    if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
+    if (on && p->ev_pool.empty()) {
+        p->ev_pool.resize(2 * 4096);
+        for (auto &e : p->ev_pool) SHTB_CUDA_TRY(cudaEventCreate(&e));
+    }
+    p->profiling = on != 0;
+    return SHTB_OK;
+}
+
+int shtb_profile_read(shtb_plan p, double *ms, int nstages, int *ncalls)
+{
+    if (!p || !ms || nstages < 0) return shtb_fail(SHTB_EINVAL, "NULL argument");
+    for (int i = 0; i < nstages; ++i) ms[i] = 0.0;
+    int calls = 0;
+    for (const auto &r : p->recs) {
+        SHTB_CUDA_TRY(cudaEventSynchronize(p->ev_pool[r.ev1]));
+        float t = 0.f;
+        SHTB_CUDA_TRY(cudaEventElapsedTime(&t, p->ev_pool[r.ev0], p->ev_pool[r.ev1]));
+        if (r.stage < nstages) ms[r.stage] += t;
+        if (r.stage == 0 || r.stage == 2) ++calls;
+    }
+    p->recs.clear();
+    p->ev_next = 0;
+    if (ncalls) *ncalls = calls;
+    return SHTB_OK;
+}
+
+int shtb_measure_fp64_peak(int device, double *dfma, double *dmma)
+{
+    if (!dfma || !dmma) return shtb_fail(SHTB_EINVAL, "NULL argument");
+    return measure_fp64_peak(device, dfma, dmma);
+}
+
+// ------------------------------------------------------- private API
+int shtb_test_legendre(shtb_plan p, const double *alm_dev, double *q_dev, int nmaps, void *stream)
+{
+    int rc = check_call(p, alm_dev, q_dev, nmaps);
+    if (rc) return rc;
+    if ((rc = ensure_ws(p, nmaps))) return rc;
+    Workspace w = carve(p, nmaps);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = launch_alm_prescale(p, (const double2 *)alm_dev, w.ap, nmaps, st))) return rc;
+    return launch_legendre_synth(p, w.ap, (double2 *)q_dev, nmaps, st);
+}
+
+int shtb_test_phi(shtb_plan p, const double *q_dev, double *map_dev, int nmaps, void *stream)
+{
+    int rc = check_call(p, q_dev, map_dev, nmaps);
+    if (rc) return rc;
+    return launch_phi_synth(p, (const double2 *)q_dev, map_dev, nmaps, (cudaStream_t)stream);
+}
+
+int shtb_test_phi_adjoint(shtb_plan p, const double *map_dev, double *q_dev, int nmaps, void *stream)
+{
+    int rc = check_call(p, map_dev, q_dev, nmaps);
+    if (rc) return rc;
+    return launch_phi_adjoint(p, map_dev, (double2 *)q_dev, nmaps, (cudaStream_t)stream);
+}
+
+int shtb_test_legendre_adjoint(shtb_plan p, const double *q_dev, double *alm_dev, int nmaps,
+                               void *stream)
+{
+    int rc = check_call(p, q_dev, alm_dev, nmaps);
+    if (rc) return rc;
+    if ((rc = ensure_ws(p, nmaps))) return rc;
+    Workspace w = carve(p, nmaps);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = launch_legendre_adjoint(p, (const double2 *)q_dev, w.aacc, nmaps, w.adj, st))) return rc;
+    return launch_alm_finish(p, w.aacc, (double2 *)alm_dev, nmaps, st);
+}
+
+}  // extern "C"

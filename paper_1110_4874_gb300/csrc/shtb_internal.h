@@ -1,0 +1,142 @@
+// Internal declarations shared by the host plan builder, the kernels and the
+// C-ABI layer.  Nothing here is part of the public interface (include/shtb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "shtb.h"
+
+// ---------------------------------------------------------------- errors
+// Record a detailed message for shtb_last_error_message() and return code.
+int shtb_fail(int code, const std::string &msg);
+
+#define SHTB_CUDA_TRY(expr)                                                            \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return shtb_fail(e_ == cudaErrorMemoryAllocation ? SHTB_ENOMEM : SHTB_ECUDA, \
+                             std::string(#expr) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+// ------------------------------------------------------------ plan layout
+// Index of coefficient (l, m) in the m-major a_lm layout.
+inline long long alm_index(int lmax, int l, int m)
+{
+    return (long long)m * (2 * lmax + 1 - m) / 2 + l;
+}
+
+// Number of l values of parity t (l - m = t mod 2) for order m: l = m+t, m+t+2, ... <= L.
+inline int chain_len(int lmax, int m, int t)
+{
+    return m + t > lmax ? 0 : (lmax - m - t) / 2 + 1;
+}
+
+// Constants of one step of the rescaled jump-two recurrence at (l, m):
+// w = mu * x + (cz or cs), V_{l+2} = w V_l - V_{l-2}; sig = sigma_l.
+struct alignas(32) RecCoef {
+    double mu, cz, cs, sig;
+};
+
+// Running state of the two parity chains of one ring (adjoint kernel).
+struct alignas(32) RecState {
+    double cur0, prev0, cur1, prev1;
+};
+
+// Everything a kernel needs to know about a plan, by value.
+struct PlanView {
+    int nside, lmax, nrings, nhalf;   // nhalf = 2 nside rings with z >= 0 (incl. equator)
+    long long npix, nalm;
+
+    // Legendre stage (Eq. three-term in the rescaled two-FMA form, see the
+    // plan builder): per (l, m) at alm_index(l, m): {mu, Cz, Cs, sigma}.
+    const RecCoef *coef;
+    // per half-ring r in [0, nhalf): signed recurrence argument and which
+    // constant (Cz or Cs) goes with it
+    const double *xarg;
+    const int *xform;
+    // start of each (m, parity, half-ring) chain after the 1e-30 crop:
+    // index ((m * 2) + t) * nhalf + r
+    const int *jstart;
+    const double2 *vstart;
+
+    // ring stage
+    const int *ring_J;               // pixels per ring
+    const int *ring_s;               // half-pixel shift flag (phi_0 = pi s / J)
+    const long long *ring_start;     // first pixel of each ring
+    const long long *ring_tw;        // offset of the ring's e^{i pi n / J} table in tw
+    const double2 *tw;
+    const int *ring_M;               // Bluestein length (0 = power-of-two ring)
+    const long long *ring_fb;        // offset of the ring's Bluestein filter in fb
+    const double2 *fb;
+    const double2 *W;                // e^{2 pi i n / Wlen}, n < Wlen
+    int Wlen;
+};
+
+struct shtb_plan_s {
+    int nside = 0, lmax = 0;
+    double eps = 0;
+    int device = 0;
+    int nrings = 0, nhalf = 0;
+    long long npix = 0, nalm = 0;
+    shtb_plan_opts opts{};
+
+    // host copies of the ring description
+    std::vector<int> ring_J, ring_s, ring_M;
+    std::vector<long long> ring_start;
+
+    // ring lists for the two FFT kernels
+    std::vector<int> pow2_rings, blue_rings;
+    int max_K_pow2 = 0, max_M_blue = 0;
+    int *d_pow2_rings = nullptr, *d_blue_rings = nullptr;
+
+    // device allocations owned by the plan (freed in destroy)
+    std::vector<void *> allocations;
+    PlanView view{};
+
+    // workspace (grown on demand)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int ws_nmaps = 0;
+
+    // statistics
+    shtb_plan_stats_t stats{};
+
+    // stage profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int stage; int ev0, ev1; };
+    std::vector<Rec> recs;
+    int ev_next = 0;
+};
+
+// ------------------------------------------------------- host plan build
+// Fills every host-side table and uploads it; defined in shtb_plan_host.cpp.
+int shtb_build_dense_plan(shtb_plan_s *p);
+
+// Device allocation helper that registers the pointer with the plan.
+int plan_alloc_upload(shtb_plan_s *p, void **dst, const void *src, size_t bytes);
+
+// ---------------------------------------------------------- kernel launches
+// shtb_legendre.cu
+int launch_alm_prescale(const shtb_plan_s *p, const double2 *alm, double2 *aprime, int nmaps,
+                        cudaStream_t st);
+int launch_legendre_synth(const shtb_plan_s *p, const double2 *aprime, double2 *q, int nmaps,
+                          cudaStream_t st);
+int launch_legendre_adjoint(const shtb_plan_s *p, const double2 *qadj, double2 *aacc,
+                            int nmaps, void *state_ws, cudaStream_t st);
+int launch_alm_finish(const shtb_plan_s *p, const double2 *aacc, double2 *alm, int nmaps,
+                      cudaStream_t st);
+size_t legendre_adjoint_state_bytes(const shtb_plan_s *p);
+
+// shtb_phi.cu
+int launch_phi_synth(const shtb_plan_s *p, const double2 *q, double *map, int nmaps,
+                     cudaStream_t st);
+int launch_phi_adjoint(const shtb_plan_s *p, const double *map, double2 *q, int nmaps,
+                       cudaStream_t st);
+
+// shtb_util.cu
+int measure_fp64_peak(int device, double *dfma, double *dmma);

@@ -1,0 +1,596 @@
+// Host-side plan builder: HEALPix ring geometry, the per-(l, m) constants of
+// the rescaled jump-two Legendre recurrence, the recurrence start values past
+// the 1e-30 crop, and the ring-FFT tables.  Everything is computed once per
+// (nside, L) in double-double where rounding matters and uploaded to the
+// device (Sec. 4.2: "the precomputation ... once"; Appendix, "Efficient code
+// for Legendre transforms").
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "shtb_dd.h"
+#include "shtb_internal.h"
+
+using shtb::DD;
+using shtb::dd;
+
+namespace {
+
+// ------------------------------------------------------------ threading
+template <class F>
+void parallel_for(int n, int nthreads, F &&fn)
+{
+    if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
+    nthreads = std::min(nthreads, std::max(n, 1));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        for (;;) {
+            int i = next.fetch_add(1);
+            if (i >= n) break;
+            fn(i);
+        }
+    };
+    if (nthreads == 1) {
+        worker();
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nthreads; ++t) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+}
+
+// -------------------------------------------- cos/sin of rational angles
+// (cos, sin)(pi * num / den) with the angle folded by integer symmetries
+// into [0, pi/4] and evaluated from a double-double argument.
+void sincospi_frac(long long num, long long den, double *c, double *s)
+{
+    long long twoden = 2 * den;
+    long long q = ((num % twoden) + twoden) % twoden;   // angle pi q/den in [0, 2pi)
+    double sc = 1.0, ss = 1.0;                          // signs for cos, sin
+    if (q >= den) { q -= den; sc = -sc; ss = -ss; }     // theta - pi
+    if (2 * q > den) { q = den - q; sc = -sc; }         // pi - theta
+    // now angle = pi q / den in [0, pi/2]; swap to the complement above pi/4
+    bool swap = 4 * q > den;
+    long long n = swap ? den - 2 * q : q;               // angle' = pi n / d
+    long long d = swap ? 2 * den : den;
+    DD a = DD{shtb::kPiHi, shtb::kPiLo} * (double)n / dd((double)d);
+    double ch = std::cos(a.hi), sh = std::sin(a.hi);
+    double cv = ch - sh * a.lo, sv = sh + ch * a.lo;
+    if (swap) std::swap(cv, sv);
+    *c = sc * cv;
+    *s = ss * sv;
+}
+
+bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+long long next_pow2(long long x)
+{
+    long long p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// In-place radix-2 decimation-in-frequency FFT with exponent sign -1:
+// natural-order input, bit-reversed output.  The device kernels use the
+// same ordering, so filters built here can be multiplied pointwise there.
+void dif_forward(std::vector<std::complex<double>> &x, const std::vector<std::complex<double>> &W,
+                 long long Wlen)
+{
+    const long long M = (long long)x.size();
+    for (long long half = M / 2; half >= 1; half /= 2) {
+        const long long stride = Wlen / (2 * half);
+        for (long long blk = 0; blk < M; blk += 2 * half) {
+            for (long long j = 0; j < half; ++j) {
+                std::complex<double> u = x[blk + j], v = x[blk + j + half];
+                std::complex<double> w = std::conj(W[j * stride]);
+                x[blk + j] = u + v;
+                x[blk + j + half] = (u - v) * w;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- geometry
+struct HalfRing {
+    double z;        // cos(theta), correctly rounded
+    double z2;       // z^2, correctly rounded from the exact ratio
+    double s2;       // sin^2(theta), correctly rounded from the exact ratio
+    double eps1;     // 1 - z, correctly rounded from the exact ratio
+    DD sdd;          // sin(theta) as dd
+};
+
+// Ring r (0-based, north to south) of the HEALPix RING grid: i = r + 1 is
+// the ring number counted from the north pole, mirrored in the south.
+//   polar i < N : z = 1 - i^2/(3N^2), J = 4i, phi_j = pi (2j + 1) / J
+//   belt        : z = (4N - 2i)/(3N), J = 4N, phi_j = pi (2j + s) / J,
+//                 s = 1 iff (i + N) is even
+HalfRing half_ring(long long N, long long i)
+{
+    long long zn, zd, sn, sd, en;
+    if (i < N) {
+        zn = 3 * N * N - i * i;
+        zd = 3 * N * N;
+        sn = i * i * (6 * N * N - i * i);
+        sd = 9 * N * N * N * N;
+        en = i * i;                 // 1 - z = i^2 / (3N^2)
+    } else {
+        zn = 4 * N - 2 * i;
+        zd = 3 * N;
+        sn = (2 * i - N) * (7 * N - 2 * i);
+        sd = 9 * N * N;
+        en = 2 * i - N;             // 1 - z = (2i - N) / (3N)
+    }
+    HalfRing h;
+    DD zq = dd((double)zn) / dd((double)zd);
+    h.z = shtb::to_double(zq);
+    h.z2 = shtb::to_double(shtb::ddmul((double)zn, (double)zn) /
+                           shtb::ddmul((double)zd, (double)zd));
+    DD s2 = dd((double)sn) / dd((double)sd);
+    h.s2 = shtb::to_double(s2);
+    h.eps1 = shtb::to_double(dd((double)en) / dd((double)zd));
+    h.sdd = shtb::sqrt(s2);
+    return h;
+}
+
+// ------------------------------------------------ recurrence constants
+// Jump-two recurrence of Eq. (three-term):
+//   P_{l+2} = ((z^2 - d_l)/c_l) P_l - (c_{l-2}/c_l) P_{l-2}
+//   c_l^m = sqrt((l-m+1)(l-m+2)(l+m+1)(l+m+2) / ((2l+1)(2l+3)^2(2l+5)))
+//   d_l^m = (2l(l+1) - 2m^2 - 1) / ((2l-1)(2l+3))
+// Rescaled by P_l = sigma_l V_l with sigma_{m+t} = sigma_{m+t+2} = 1 and
+// sigma_{l+2} = sigma_{l-2} c_{l-2} / c_l, it becomes
+//   V_{l+2} = mu_l (z^2 - d_l) V_l - V_{l-2},   mu_l = sigma_l / (c_{l-2} sigma_{l-2}),
+// two FMAs per step: w = mu_l x + C, V_{l+2} = w V_l - V_{l-2} with
+// (x, C) = (z^2, -mu_l d_l) or (-sin^2, mu_l (1 - d_l)).  The sin^2 form keeps
+// the argument exact near the poles, where z^2 rounded to a double would
+// move theta by up to 1e-10 relative at Nside = 2048.
+DD c_coef(long long l, long long m)
+{
+    DD num = shtb::ddmul((double)((l - m + 1) * (l - m + 2)), (double)((l + m + 1) * (l + m + 2)));
+    DD den = shtb::ddmul((double)((2 * l + 1) * (2 * l + 5)), (double)((2 * l + 3) * (2 * l + 3)));
+    return shtb::sqrt(num / den);
+}
+
+DD d_coef(long long l, long long m)
+{
+    return dd((double)(2 * l * (l + 1) - 2 * m * m - 1)) / dd((double)((2 * l - 1) * (2 * l + 3)));
+}
+
+DD one_minus_d(long long l, long long m)
+{
+    return dd((double)(2 * (l * l + l - 1 + m * m))) / dd((double)((2 * l - 1) * (2 * l + 3)));
+}
+
+void build_coefficients(int L, int m, RecCoef *out /* indexed by l - m */)
+{
+    for (int t = 0; t < 2; ++t) {
+        const int n = chain_len(L, m, t);
+        if (n == 0) continue;
+        // chain j: l_j = m + t + 2j
+        std::vector<DD> c(n), sig(n);
+        for (int j = 0; j < n; ++j) c[j] = c_coef(m + t + 2 * j, m);
+        sig[0] = dd(1.0);
+        if (n > 1) sig[1] = dd(1.0);
+        for (int j = 1; j + 1 < n; ++j) sig[j + 1] = sig[j - 1] * c[j - 1] / c[j];
+        for (int j = 0; j < n; ++j) {
+            const int l = m + t + 2 * j;
+            RecCoef e;
+            e.sig = shtb::to_double(sig[j]);
+            if (j >= 1) {
+                DD mu = sig[j] / (c[j - 1] * sig[j - 1]);
+                e.mu = shtb::to_double(mu);
+                e.cz = shtb::to_double(-(mu * d_coef(l, m)));
+                e.cs = shtb::to_double(mu * one_minus_d(l, m));
+            } else {
+                e.mu = e.cz = e.cs = 0.0;   // first element of a chain: no step starts there
+            }
+            out[l - m] = e;
+        }
+    }
+}
+
+// c_m = sqrt(1/(4 pi) prod_{i=1}^m (2i+1)/(2i)) as dd, m = 0..L
+std::vector<DD> diag_norms(int L)
+{
+    std::vector<DD> out(L + 1);
+    DD c2 = dd(1.0) / (DD{shtb::kPiHi, shtb::kPiLo} * 4.0);
+    out[0] = shtb::sqrt(c2);
+    for (int i = 1; i <= L; ++i) {
+        c2 = c2 * (dd(2.0 * i + 1.0) / dd(2.0 * i));
+        out[i] = shtb::sqrt(c2);
+    }
+    return out;
+}
+
+// x^m as (mantissa dd in [0.5,1), exponent) by binary powering
+DD dd_pow(DD x, int m, int *E)
+{
+    auto norm = [](DD v, int *e) {
+        int k;
+        std::frexp(v.hi, &k);
+        *e += k;
+        return DD{std::ldexp(v.hi, -k), std::ldexp(v.lo, -k)};
+    };
+    DD r = dd(1.0), b = x;
+    int er = 0, eb = 0;
+    b = norm(b, &eb);
+    while (m > 0) {
+        if (m & 1) { r = r * b; er += eb; r = norm(r, &er); }
+        m >>= 1;
+        if (m) { b = b * b; eb *= 2; b = norm(b, &eb); }
+    }
+    *E = er;
+    return r;
+}
+
+constexpr double kCrop = 1e-30;   // Appendix: values below 1e-30 are neglected
+
+// b_l = sqrt((l^2 - m^2)/(4 l^2 - 1)) for l = m+1..L (index l - m) of the
+// textbook one-step recurrence Ptilde_l = (z Ptilde_{l-1} - b_{l-1} Ptilde_{l-2}) / b_l
+std::vector<double> one_step_coefs(int L, int m)
+{
+    std::vector<double> b(L - m + 2, 0.0);
+    for (int l = m + 1; l <= L; ++l)
+        b[l - m] = std::sqrt(((double)(l - m) * (double)(l + m)) /
+                             ((double)(2 * l - 1) * (double)(2 * l + 1)));
+    return b;
+}
+
+// For order m at one half-ring: per parity t the first chain index js[t]
+// with |Ptilde_{m+t+2j}^m| >= 1e-30 and the rescaled values V = Ptilde/sigma
+// there and one chain step later (js[t] = chain length if none).  Found by
+// the one-step recurrence in l from Ptilde_m^m = (-1)^m c_m sin^m(theta),
+// with a separate power-of-two exponent so that nothing underflows; near the
+// poles z*P is formed as P - (1-z) P so that 1 - z enters exactly.
+void chain_starts(int L, int m, const HalfRing &h, DD cm, const std::vector<double> &b,
+                  const RecCoef *cf, int js[2], double2 vs[2])
+{
+    const int n0 = chain_len(L, m, 0), n1 = chain_len(L, m, 1);
+    const double sq = std::sqrt(2.0 * m + 3.0);
+    const bool near_pole = h.z > 0.5;
+    auto zmul = [&](double v) { return near_pole ? v - h.eps1 * v : h.z * v; };
+    js[0] = js[1] = -1;
+    double v0[2] = {0, 0}, v1[2] = {0, 0};
+    bool res[2] = {n0 == 0, n1 == 0};   // chain resolved
+    int E = 0;
+    DD pm = dd_pow(h.sdd, m, &E) * cm;
+    double P0 = shtb::to_double(pm);
+    if (m & 1) P0 = -P0;
+    double P1 = 0.0;
+    auto visit = [&](int l, double Pm) {   // Pm: mantissa at exponent E
+        const int t = (l - m) & 1;
+        if (res[t]) return;
+        const int j = (l - m - t) / 2;
+        const double v = E == 0 ? Pm : std::ldexp(Pm, E);
+        if (js[t] < 0) {
+            if (std::fabs(v) >= kCrop) {
+                js[t] = j;
+                v0[t] = v;
+                if (l + 2 > L) res[t] = true;
+            }
+        } else {                            // the chain's next element
+            v1[t] = v;
+            res[t] = true;
+        }
+    };
+    visit(m, P0);
+    if (m < L) {
+        P1 = sq * zmul(P0);
+        visit(m + 1, P1);
+    }
+    for (int l = m + 2; l <= L && !(res[0] && res[1]); ++l) {
+        double P2 = (zmul(P1) - b[l - 1 - m] * P0) / b[l - m];
+        P0 = P1;
+        P1 = P2;
+        if (E != 0 && P1 != 0.0) {
+            int k;
+            std::frexp(P1, &k);
+            if (k + E > -900) {
+                P0 = std::ldexp(P0, E);
+                P1 = std::ldexp(P1, E);
+                E = 0;
+            } else if (k > 600) {
+                P0 = std::ldexp(P0, -512);
+                P1 = std::ldexp(P1, -512);
+                E += 512;
+            }
+        }
+        visit(l, P1);
+    }
+    for (int t = 0; t < 2; ++t) {
+        const int nt = t == 0 ? n0 : n1;
+        if (js[t] < 0 || nt == 0) {
+            js[t] = nt;                          // nothing above the crop
+            vs[t] = make_double2(0.0, 0.0);
+        } else {
+            const int l0 = m + t + 2 * js[t];
+            const double s0 = cf[l0 - m].sig;
+            const double s1 = l0 + 2 <= L ? cf[l0 + 2 - m].sig : 1.0;
+            vs[t] = make_double2(v0[t] / s0, l0 + 2 <= L ? v1[t] / s1 : 0.0);
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+int plan_alloc_upload(shtb_plan_s *p, void **dst, const void *src, size_t bytes)
+{
+    void *d = nullptr;
+    size_t nb = bytes ? bytes : 16;
+    cudaError_t e = cudaMalloc(&d, nb);
+    if (e != cudaSuccess)
+        return shtb_fail(SHTB_ENOMEM, std::string("cudaMalloc plan table: ") + cudaGetErrorString(e));
+    p->allocations.push_back(d);
+    if (src && bytes) {
+        e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return shtb_fail(SHTB_ECUDA, std::string("cudaMemcpy plan table: ") + cudaGetErrorString(e));
+    }
+    p->stats.plan_device_bytes += (long long)nb;
+    *dst = d;
+    return SHTB_OK;
+}
+
+int shtb_build_dense_plan(shtb_plan_s *p)
+{
+    const int N = p->nside, L = p->lmax;
+    const int nthreads = p->opts.nthreads;
+    const int Z = 2 * N;   // rings with z >= 0, equator last
+    p->nhalf = Z;
+    p->nrings = 4 * N - 1;
+    p->npix = 12LL * N * N;
+    p->nalm = (long long)(L + 1) * (L + 2) / 2;
+
+    // ---------------------------------------------------------- geometry
+    std::vector<HalfRing> hr(Z);
+    std::vector<double> xarg(Z);
+    std::vector<int> xform(Z);
+    for (int r = 0; r < Z; ++r) {
+        hr[r] = half_ring(N, r + 1);
+        if (hr[r].s2 < 0.5) { xarg[r] = -hr[r].s2; xform[r] = 1; }
+        else { xarg[r] = hr[r].z2; xform[r] = 0; }
+    }
+    p->ring_J.resize(p->nrings);
+    p->ring_s.resize(p->nrings);
+    p->ring_start.resize(p->nrings);
+    long long pix = 0;
+    for (int r = 0; r < p->nrings; ++r) {
+        long long i = r < Z ? r + 1 : 4LL * N - (r + 1);
+        p->ring_J[r] = (int)(i < N ? 4 * i : 4LL * N);
+        p->ring_s[r] = i < N ? 1 : (((i + N) % 2 == 0) ? 1 : 0);
+        p->ring_start[r] = pix;
+        pix += p->ring_J[r];
+    }
+
+    // --------------------------------------- recurrence constants (Eq. three-term)
+    std::vector<RecCoef> coef((size_t)p->nalm);
+    parallel_for(L + 1, nthreads, [&](int m) {
+        build_coefficients(L, m, coef.data() + alm_index(L, m, m));
+    });
+
+    // --------------------------------------------- start values past the crop
+    // For each (m, parity t, half-ring r): first chain index j with
+    // |Ptilde_{m+t+2j}^m(z_r)| >= 1e-30 and the rescaled values V there and
+    // one chain step later.  Found by the one-step recurrence in l from
+    // Ptilde_m^m = (-1)^m c_m sin^m(theta), carried with a separate
+    // power-of-two exponent so that nothing underflows.
+    const std::vector<DD> cm = diag_norms(L);
+    std::vector<int> jstart((size_t)(L + 1) * 2 * Z);
+    std::vector<double2> vstart((size_t)(L + 1) * 2 * Z);
+    parallel_for(L + 1, nthreads, [&](int m) {
+        const std::vector<double> b = one_step_coefs(L, m);
+        const RecCoef *cf = coef.data() + alm_index(L, m, m);
+        for (int r = 0; r < Z; ++r) {
+            int js[2];
+            double2 vs[2];
+            chain_starts(L, m, hr[r], cm[m], b, cf, js, vs);
+            for (int t = 0; t < 2; ++t) {
+                const size_t idx = ((size_t)m * 2 + t) * Z + r;
+                jstart[idx] = js[t];
+                vstart[idx] = vs[t];
+            }
+        }
+    });
+
+    // statistics of the recurrence work
+    long long n_rec = 0, n_exec = 0;
+    const int nchunk = (Z + 31) / 32;
+    for (int m = 0; m <= L; ++m) {
+        const int n0 = chain_len(L, m, 0), n1 = chain_len(L, m, 1);
+        for (int c = 0; c < nchunk; ++c) {
+            int jlo = n0;
+            for (int r = c * 32; r < std::min(Z, c * 32 + 32); ++r) {
+                for (int t = 0; t < 2; ++t) {
+                    const int nt = t == 0 ? n0 : n1;
+                    int j = jstart[((size_t)m * 2 + t) * Z + r];
+                    n_rec += nt - j;
+                    if (j < nt) jlo = std::min(jlo, j);
+                }
+            }
+            if (jlo < n0) n_exec += 32LL * ((n0 - jlo) + std::max(0, n1 - jlo));
+        }
+    }
+    p->stats.n_recurrence = n_rec;
+    p->stats.n_recurrence_exec = n_exec;
+    p->stats.recurrence_flops = 4.0 * (double)n_rec;
+    p->stats.legendre_flops_per_map = 4.0 * (double)n_rec;
+
+    // ------------------------------------------------------- ring FFT tables
+    // Per ring: K = J/2 (J is always even); K a power of two -> in-place
+    // radix-2 FFT, otherwise Bluestein with M = next_pow2(2K - 1).
+    p->ring_M.assign(p->nrings, 0);
+    std::vector<long long> ring_tw(p->nrings), ring_fb(p->nrings, -1);
+    p->pow2_rings.clear();
+    p->blue_rings.clear();
+    p->max_K_pow2 = 0;
+    p->max_M_blue = 0;
+    long long Wlen = 2;
+    for (int r = 0; r < p->nrings; ++r) {
+        long long K = p->ring_J[r] / 2;
+        if (is_pow2(K)) {
+            p->pow2_rings.push_back(r);
+            p->max_K_pow2 = std::max<long long>(p->max_K_pow2, K);
+            Wlen = std::max(Wlen, K);
+        } else {
+            long long M = next_pow2(2 * K - 1);
+            p->ring_M[r] = (int)M;
+            p->blue_rings.push_back(r);
+            p->max_M_blue = std::max<long long>(p->max_M_blue, M);
+            Wlen = std::max(Wlen, M);
+        }
+    }
+    if ((long long)std::max(p->max_K_pow2, p->max_M_blue) * 16 > 200 * 1024)
+        return shtb_fail(SHTB_ENOTSUP, "ring FFT does not fit in shared memory (nside too large)");
+
+    // e^{i pi n / J} tables, one per distinct J (north and south rings share)
+    std::vector<double2> tw;
+    std::vector<long long> tw_of_J(4 * N + 1, -1);
+    for (int r = 0; r < p->nrings; ++r) {
+        int J = p->ring_J[r];
+        if (tw_of_J[J] < 0) {
+            tw_of_J[J] = (long long)tw.size();
+            for (int n = 0; n < J; ++n) {
+                double c, s;
+                sincospi_frac(n, J, &c, &s);
+                tw.push_back(make_double2(c, s));
+            }
+        }
+        ring_tw[r] = tw_of_J[J];
+    }
+    // e^{2 pi i n / Wlen}
+    std::vector<double2> W(Wlen);
+    std::vector<std::complex<double>> Wc(Wlen);
+    for (long long n = 0; n < Wlen; ++n) {
+        double c, s;
+        sincospi_frac(2 * n, Wlen, &c, &s);
+        W[n] = make_double2(c, s);
+        Wc[n] = {c, s};
+    }
+    // Bluestein filters: for the positive-exponent DFT of length K,
+    //   X_n = c_n sum_k (Z_k c_k) conj(c_{n-k}),  c_j = e^{i pi j^2 / K},
+    // as a cyclic convolution of length M with b_j = conj(c_j) (|j| < K);
+    // stored as DIF_forward(b) / M in bit-reversed order.
+    std::vector<long long> fb_of_J(4 * N + 1, -1);
+    std::vector<int> distinct;
+    for (int r : p->blue_rings)
+        if (fb_of_J[p->ring_J[r]] < 0) { fb_of_J[p->ring_J[r]] = 0; distinct.push_back(p->ring_J[r]); }
+    std::vector<long long> fb_off(distinct.size());
+    long long fb_total = 0;
+    for (size_t d = 0; d < distinct.size(); ++d) {
+        fb_off[d] = fb_total;
+        fb_of_J[distinct[d]] = fb_total;
+        fb_total += next_pow2(2 * (distinct[d] / 2) - 1);
+    }
+    std::vector<double2> fb((size_t)fb_total);
+    parallel_for((int)distinct.size(), nthreads, [&](int d) {
+        const long long K = distinct[d] / 2, M = next_pow2(2 * K - 1);
+        std::vector<std::complex<double>> bv(M, 0.0);
+        for (long long j = 0; j < K; ++j) {
+            double c, s;
+            sincospi_frac((j * j) % (2 * K), K, &c, &s);
+            std::complex<double> v(c, -s);
+            bv[j] = v;
+            if (j > 0) bv[M - j] = v;
+        }
+        dif_forward(bv, Wc, Wlen);
+        for (long long k = 0; k < M; ++k)
+            fb[fb_off[d] + k] = make_double2(bv[k].real() / M, bv[k].imag() / M);
+    });
+    for (int r : p->blue_rings) ring_fb[r] = fb_of_J[p->ring_J[r]];
+
+    // algorithmic FFT flops: 2.5 J log2 J per real ring transform of length J
+    double phi_flops = 0.0;
+    for (int r = 0; r < p->nrings; ++r)
+        phi_flops += 2.5 * p->ring_J[r] * std::log2((double)p->ring_J[r]);
+    p->stats.phi_flops_per_map = phi_flops;
+
+    // --------------------------------------------------------------- upload
+    PlanView &v = p->view;
+    v.nside = N;
+    v.lmax = L;
+    v.nrings = p->nrings;
+    v.nhalf = Z;
+    v.npix = p->npix;
+    v.nalm = p->nalm;
+    v.Wlen = (int)Wlen;
+    int rc;
+#define UP(field, vec)                                                                  \
+    do {                                                                                \
+        void *d_;                                                                       \
+        rc = plan_alloc_upload(p, &d_, (vec).data(), sizeof((vec)[0]) * (vec).size());  \
+        if (rc) return rc;                                                              \
+        v.field = (decltype(v.field))d_;                                                \
+    } while (0)
+    UP(coef, coef);
+    UP(xarg, xarg);
+    UP(xform, xform);
+    UP(jstart, jstart);
+    UP(vstart, vstart);
+    UP(ring_J, p->ring_J);
+    UP(ring_s, p->ring_s);
+    UP(ring_start, p->ring_start);
+    UP(ring_tw, ring_tw);
+    UP(tw, tw);
+    UP(ring_M, p->ring_M);
+    UP(ring_fb, ring_fb);
+    UP(fb, fb);
+    UP(W, W);
+#undef UP
+    void *d;
+    rc = plan_alloc_upload(p, &d, p->pow2_rings.data(), sizeof(int) * p->pow2_rings.size());
+    if (rc) return rc;
+    p->d_pow2_rings = (int *)d;
+    rc = plan_alloc_upload(p, &d, p->blue_rings.data(), sizeof(int) * p->blue_rings.size());
+    if (rc) return rc;
+    p->d_blue_rings = (int *)d;
+
+    // bytes one call reads from the plan (Legendre tables + start values)
+    p->stats.plan_read_bytes = (long long)(sizeof(RecCoef) * coef.size() + sizeof(int) * jstart.size() +
+                                           sizeof(double2) * vstart.size());
+    return SHTB_OK;
+}
+
+// ------------------------------------------------------------------------
+// Private host-only check of the plan tables (no GPU): Ptilde_l^m at HEALPix
+// half-ring r (0-based from the north pole) for l = m..lmax, evaluated with
+// exactly the tables and the two-FMA step the kernels use.
+extern "C" int shtb_test_host_recurrence(int nside, int lmax, int m, int r, double *out)
+{
+    if (nside < 1 || lmax < 0 || m < 0 || m > lmax || r < 0 || r >= 2 * nside || !out)
+        return shtb_fail(SHTB_EINVAL, "bad arguments");
+    const HalfRing h = half_ring(nside, r + 1);
+    std::vector<RecCoef> cf(lmax - m + 1);
+    build_coefficients(lmax, m, cf.data());
+    const std::vector<DD> cm = diag_norms(lmax);
+    const std::vector<double> b = one_step_coefs(lmax, m);
+    int js[2];
+    double2 vs[2];
+    chain_starts(lmax, m, h, cm[m], b, cf.data(), js, vs);
+    const bool sform = h.s2 < 0.5;
+    const double x = sform ? -h.s2 : h.z2;
+    for (int l = m; l <= lmax; ++l) out[l - m] = 0.0;
+    for (int t = 0; t < 2; ++t) {
+        const int n = chain_len(lmax, m, t);
+        double cur = 0.0, prev = 0.0;
+        for (int j = js[t]; j < n; ++j) {
+            const int l = m + t + 2 * j;
+            double nxt;
+            if (j == js[t]) { cur = vs[t].x; nxt = vs[t].y; }
+            else {
+                const RecCoef &c = cf[l - m];
+                const double w = std::fma(c.mu, x, sform ? c.cs : c.cz);
+                nxt = std::fma(w, cur, -prev);
+            }
+            out[l - m] = cf[l - m].sig * cur;
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    return SHTB_OK;
+}
