@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of HEALPix spherical-harmonic synthesis at Planck resolution.
+
+Workload: Nside = 2048 (50,331,648 pixels, 8191 rings), L = 4096, a batch of
+8 maps of seeded Gaussian a_lm (Re, Im ~ N(0, C_l/2), C_l = 1/(l+1)^2), FP64,
+requested accuracy eps = 1e-10.  A step is one synthesis of the whole batch
+(Legendre stage + ring FFT stage) on inputs already resident in HBM; the
+adjoint of the same batch and the plain one-map-per-launch synthesis are
+timed the same way and reported beside it.  Inputs (1.07 GB of a_lm, 3.2 GB
+of maps, 4.3 GB of q) are far larger than the 129 MB L2, so no flush is
+needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (the transform is replicated, not sharded); value is
+the whole-job ms per map: the slowest rank's time over all maps of all
+ranks.  ``--impl reference`` times the CPU oracle (the only reference
+implementation: the paper ships no code) on a bounded ring sample of the
+same workload and extrapolates to ms per map.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L=4096 HEALPix synthesis ms/map, % HBM roofline; batched & adjoint vs plain"
+UNIT = "ms/map"
+
+# GB300 FP64 pipe: 152 SMs x 2 DFMA/clock/SM x 2 flop x 2.070 GHz max SM clock
+# (2 DFMA/clock/SM is NVIDIA's published 1.25 TFLOP/s FP64 rate for GB300
+# divided over 152 SMs at 2070 MHz).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# DRAM traffic of the dominant kernel from an ncu capture (see profiles/);
+# valid only while the kernel source is unchanged.
+NCU_TRAFFIC = {
+    "kernel": "legendre_synth_kernel<8>",
+    "source": "paper_1110_4874_gb300/csrc/shtb_legendre.cu",
+    "source_sha256": "2716a9eb2679dc0a7730c490c671b800e69d7688a7fb6465ffbe4592e8d7cacb",
+    # 410.5 MB measured at Nside=512, L=1024; every array scales with Nside*L (x16)
+    "bytes_per_launch": 16 * 410_475_008,
+    "profile": "profiles/legendre_synth_nside512_l1024_b8.md",
+}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def file_sha256(path):
+    with open(os.path.join(ROOT, path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+# ------------------------------------------------------------ clock sampling
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi every 200 ms while the timed region runs."""
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(nside, lmax, nmaps_sample, nrings_sample, seed, nthreads=0):
+    """Time the CPU oracle on a ring sample of one map and extrapolate to ms
+    per map (cost per ring scales with the ring count of the sample)."""
+    import numpy as np
+
+    import oracle
+    from paper_1110_4874_gb300 import synthetic
+
+    rings = oracle.healpix_rings(nside)
+    idx = np.unique(np.linspace(0, rings.nrings - 1, nrings_sample).round().astype(int))
+    sub = rings.subset(idx)
+    a = synthetic.gaussian_alm(lmax, nmaps_sample, seed=seed)
+    t0 = time.perf_counter()
+    oracle.synthesize(sub, lmax, a, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    ms_per_map = dt * 1e3 / nmaps_sample * rings.nrings / idx.size
+    cores = nthreads if nthreads > 0 else oracle.max_threads()
+    sample = (f"{idx.size} of {rings.nrings} rings (evenly spaced, poles and equator included) "
+              f"of {nmaps_sample} map(s), oracle synthesis (double-double one-step Legendre "
+              f"recurrence + direct per-ring DFT), {dt:.1f} s, scaled by {rings.nrings}/{idx.size}")
+    return ms_per_map, cores, sample
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import paper_1110_4874_gb300 as sh
+    from paper_1110_4874_gb300 import synthetic
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, L, B = args.nside, args.lmax, args.nmaps
+
+    t0 = time.perf_counter()
+    eps_plan = args.eps
+    try:
+        plan = sh.Plan(N, L, eps_plan)
+    except sh.ShtbError as e:
+        if e.code != sh.SHTB_ENOTSUP or eps_plan <= 0:
+            raise
+        eps_plan = 0.0                      # compressed plans unavailable: exact operator
+        plan = sh.Plan(N, L, eps_plan)
+    plan_s = time.perf_counter() - t0
+    st = plan.stats()
+    plan.reserve(B)
+
+    alm_h = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=2000 + 100 * rank)).pin_memory()
+    alm = alm_h.to(dev)
+    maps = torch.empty((B, plan.npix), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    synth = lambda: plan.synthesize(alm, out=maps)  # noqa: E731
+    for _ in range(args.warmup):
+        synth()
+    # ---- headline: batched synthesis, with stage events for the roofline
+    sh.shtb_profile_enable(plan.handle, True)
+    sh.shtb_profile_read(plan.handle)
+    launches0 = plan.stats()["kernel_launches"]
+    with ClockSampler(local) as clk:
+        ms_total = timed(synth, args.steps)
+    launches = plan.stats()["kernel_launches"] - launches0
+    stages, ncalls = sh.shtb_profile_read(plan.handle)
+    sh.shtb_profile_enable(plan.handle, False)
+    clocks = clk.summary()
+    value = ms_total / (args.steps * B * world)
+
+    # ---- adjoint of the same batch
+    f = torch.from_numpy(synthetic.gaussian_map(plan.npix, B, seed=3000 + rank)).to(dev)
+    aout = torch.empty((B, plan.nalm), dtype=torch.complex128, device=dev)
+    adj = lambda: plan.adjoint(f, out=aout)  # noqa: E731
+    adj()
+    ms_adj = timed(adj, args.steps) / (args.steps * B * world)
+
+    # ---- plain: one map per launch
+    def plain():
+        for b in range(B):
+            plan.synthesize(alm[b:b + 1], out=maps[b:b + 1])
+    plain()
+    ms_plain = timed(plain, args.steps) / (args.steps * B * world)
+
+    # ---- end to end through the C ABI with host buffers (copies inside)
+    maps_h = torch.empty((B, plan.npix), dtype=torch.float64).pin_memory()
+    sh.shtb_synthesize_host(plan.handle, alm_h, maps_h, B)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sh.shtb_synthesize_host(plan.handle, alm_h, maps_h, B)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": e2e_s * 1e3 / (args.steps * B * world), "unit": UNIT,
+           "h2d_bytes_per_step": int(alm_h.numel() * alm_h.element_size()),
+           "d2h_bytes_per_step": int(maps_h.numel() * maps_h.element_size())}
+
+    # ---- roofline of the dominant kernel (the Legendre stage, FP64-bound)
+    leg_ms = stages["legendre_synth"] / max(ncalls, 1)
+    groups = [8] * (B // 8) + ([B % 8] if B % 8 else [])
+    flops = sum(4.0 * st["n_recurrence"] * (1 + g) for g in groups)   # 2 FMA/step + 2 FMA/map
+    achieved = flops / (leg_ms * 1e-3) / 1e12
+    traffic = None
+    if NCU_TRAFFIC["bytes_per_launch"] and NCU_TRAFFIC["source_sha256"] == file_sha256(NCU_TRAFFIC["source"]):
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "kernel": "legendre_synth_kernel (FP64 pipe)",
+                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+    # whole-step HBM view (algorithmic bytes of the batch over the step time)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    step_bytes = (st["plan_read_bytes"] + B * st["nalm"] * 16 * 3 + B * plan.nrings * (L + 1) * 16 * 2
+                  + B * plan.npix * 8)
+    step_ms = ms_total / args.steps
+    hbm = {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (step_ms * 1e-3) / 1e9, 1),
+           "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)" if hbm_peak else None,
+           "frac": round(step_bytes / (step_ms * 1e-3) / 1e9 / hbm_peak, 4) if hbm_peak else None}
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Gaussian a_lm, C_l = 1/(l+1)^2)",
+        "config": {"workload": f"HEALPix synthesis Nside={N} L={L} batch of {B} maps",
+                   "nside": N, "lmax": L, "nmaps": B, "eps_requested": args.eps,
+                   "eps_plan": eps_plan, "compressed": bool(st["compressed"]),
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (1.07 GB a_lm, 3.2 GB maps per 8 maps)"},
+        "roofline": roofline, "hbm": hbm, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks,
+        "details": {"adjoint_ms_per_map": round(ms_adj, 4), "plain_ms_per_map": round(ms_plain, 4),
+                    "batched_over_plain": round(ms_plain / value, 3),
+                    "stage_ms_per_step": {k: round(v / max(ncalls, 1), 3) for k, v in stages.items() if v},
+                    "plan_build_s": round(plan_s, 2),
+                    "plan_device_gb": round(st["plan_device_bytes"] / 1e9, 3),
+                    "n_recurrence": st["n_recurrence"], "n_dense": st["n_dense"],
+                    "legendre_flops_per_launch": flops},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms_cpu, cores, sample = oracle_sample(N, L, 1, args.cpu_rings, seed=2000)
+        out["cpu_baseline"] = {"value": round(ms_cpu, 1), "unit": UNIT, "cores": cores,
+                               "kind": "oracle", "sample": sample}
+    plan.close()
+    return out
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step a bounded ring sample."""
+    vals = []
+    cores, sample = None, None
+    for _ in range(args.warmup):
+        oracle_sample(args.nside, args.lmax, 1, max(4, args.ref_rings // 4), seed=2000)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        v, cores, sample = oracle_sample(args.nside, args.lmax, 1, args.ref_rings, seed=2000 + s)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall * 1e3 / args.steps, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Gaussian a_lm, C_l = 1/(l+1)^2)", "impl": "reference",
+        "config": {"workload": f"HEALPix synthesis Nside={args.nside} L={args.lmax} batch of {args.nmaps} maps",
+                   "nside": args.nside, "lmax": args.lmax, "nmaps": args.nmaps,
+                   "eps_requested": args.eps},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nside", type=int, default=2048)
+    ap.add_argument("--lmax", type=int, default=4096)
+    ap.add_argument("--nmaps", type=int, default=8)
+    ap.add_argument("--eps", type=float, default=1e-10)
+    ap.add_argument("--cpu-rings", type=int, default=64, help="ring sample of the CPU baseline")
+    ap.add_argument("--ref-rings", type=int, default=16, help="ring sample per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    out = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
