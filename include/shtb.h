@@ -94,6 +94,7 @@ typedef struct {
     double recurrence_flops;        /* FP64 flops of the recurrence per call           */
     double phi_flops_per_map;       /* FP64 flops of the ring FFT stage per map       */
     double build_seconds;           /* host + device time of shtb_plan_create         */
+    long long kernel_launches;      /* CUDA kernels this plan has launched so far     */
     int depth_hist[16];             /* (m, parity) count per butterfly depth          */
 } shtb_plan_stats_t;
 

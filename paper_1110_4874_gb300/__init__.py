@@ -54,7 +54,8 @@ class PlanStats(ctypes.Structure):
                 ("n_rstored", ctypes.c_longlong), ("plan_device_bytes", ctypes.c_longlong),
                 ("plan_read_bytes", ctypes.c_longlong), ("legendre_flops_per_map", ctypes.c_double),
                 ("recurrence_flops", ctypes.c_double), ("phi_flops_per_map", ctypes.c_double),
-                ("build_seconds", ctypes.c_double), ("depth_hist", ctypes.c_int * 16)]
+                ("build_seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+                ("depth_hist", ctypes.c_int * 16)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "depth_hist"}
@@ -144,11 +145,24 @@ def _dptr(t, dtype, name):
 
 
 # ------------------------------------------------------------- C-ABI names
+def shtb_plan_opts_init() -> PlanOpts:
+    opts = PlanOpts()
+    _check(lib().shtb_plan_opts_init(ctypes.byref(opts)), "shtb_plan_opts_init")
+    return opts
+
+
+def shtb_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def shtb_last_error_message() -> str:
+    return lib().shtb_last_error_message().decode()
+
+
 def shtb_plan_create(nside: int, lmax: int, eps: float = 0.0, leaf_cols: int = 32,
                      max_depth: int = -1, rho: float = 0.0, nthreads: int = 0,
                      device: int = -1) -> ctypes.c_void_p:
-    opts = PlanOpts()
-    _check(lib().shtb_plan_opts_init(ctypes.byref(opts)), "shtb_plan_opts_init")
+    opts = shtb_plan_opts_init()
     opts.leaf_cols, opts.max_depth, opts.rho = leaf_cols, max_depth, rho
     opts.nthreads, opts.device = nthreads, device
     h = ctypes.c_void_p()
