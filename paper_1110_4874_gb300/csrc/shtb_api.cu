@@ -266,6 +266,7 @@ int shtb_plan_destroy(shtb_plan p)
 int shtb_plan_stats(shtb_plan p, shtb_plan_stats_t *out)
 {
     if (!p || !out) return shtb_fail(SHTB_EINVAL, "NULL argument");
+    p->stats.kernel_launches = p->launches;
     *out = p->stats;
     return SHTB_OK;
 }

@@ -104,6 +104,7 @@ struct shtb_plan_s {
 
     // statistics
     shtb_plan_stats_t stats{};
+    mutable long long launches = 0;   // kernels launched on behalf of this plan
 
     // stage profiling
     bool profiling = false;

@@ -354,6 +354,7 @@ int launch_adjoint_nb(const shtb_plan_s *p, const double2 *g, double2 *aacc, Rec
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     legendre_adjoint_kernel<NB><<<p->lmax + 1, 32 * kAdjWarps, smem, st>>>(p->view, g, aacc, state,
                                                                            nmaps, b0);
+    ++p->launches;
     SHTB_CUDA_TRY(cudaGetLastError());
     return SHTB_OK;
 }
@@ -364,6 +365,7 @@ int launch_alm_prescale(const shtb_plan_s *p, const double2 *alm, double2 *ap, i
                         cudaStream_t st)
 {
     alm_prescale_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ap, nmaps);
+    ++p->launches;
     SHTB_CUDA_TRY(cudaGetLastError());
     return SHTB_OK;
 }
@@ -391,6 +393,7 @@ int launch_legendre_synth(const shtb_plan_s *p, const double2 *ap, double2 *q, i
             b0 += 1;
         }
         SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
     }
     return SHTB_OK;
 }
@@ -407,6 +410,7 @@ int launch_legendre_adjoint(const shtb_plan_s *p, const double2 *qadj, double2 *
     double2 *g = (double2 *)ws;
     RecState *state = (RecState *)(g + (size_t)(p->lmax + 1) * 2 * p->nhalf * nmaps);
     adjoint_parity_kernel<<<dim3(p->nhalf, nmaps), 256, 0, st>>>(p->view, qadj, g, nmaps);
+    ++p->launches;
     SHTB_CUDA_TRY(cudaGetLastError());
     for (int b0 = 0; b0 < nmaps;) {
         const int left = nmaps - b0;
@@ -424,6 +428,7 @@ int launch_alm_finish(const shtb_plan_s *p, const double2 *aacc, double2 *alm, i
                       cudaStream_t st)
 {
     alm_finish_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, aacc, alm, nmaps);
+    ++p->launches;
     SHTB_CUDA_TRY(cudaGetLastError());
     return SHTB_OK;
 }

@@ -224,6 +224,7 @@ int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int 
                 p->view, p->d_pow2_rings, (const double *)in, (double2 *)out);
         }
         SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
     }
     if (!p->blue_rings.empty()) {
         const size_t smem = sizeof(double2) * (size_t)p->max_M_blue;
@@ -240,6 +241,7 @@ int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int 
                 p->view, p->d_blue_rings, (const double *)in, (double2 *)out);
         }
         SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
     }
     return SHTB_OK;
 }

@@ -11,6 +11,7 @@
 namespace {
 
 constexpr int kIters = 4096;
+constexpr int kReps = 10;
 
 __global__ void dfma_peak_kernel(double *out, double a, double b)
 {
@@ -65,25 +66,26 @@ int measure_fp64_peak(int device, double *dfma, double *dmma)
     const int blocks = nsm * 8, threads = 256;
     float ms = 0.f;
 
-    dfma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
+    // warm-up long enough for the clocks to settle, then time several launches
+    for (int i = 0; i < 20; ++i) dfma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
     SHTB_CUDA_TRY(cudaGetLastError());
     SHTB_CUDA_TRY(cudaEventRecord(e0));
-    dfma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
+    for (int i = 0; i < kReps; ++i) dfma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
     SHTB_CUDA_TRY(cudaEventRecord(e1));
     SHTB_CUDA_TRY(cudaEventSynchronize(e1));
     SHTB_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    *dfma = 2.0 * 8.0 * kIters * (double)blocks * threads / (ms * 1e-3) / 1e9;
+    *dfma = kReps * 2.0 * 8.0 * kIters * (double)blocks * threads / (ms * 1e-3) / 1e9;
 
-    dmma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
+    for (int i = 0; i < 5; ++i) dmma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
     SHTB_CUDA_TRY(cudaGetLastError());
     SHTB_CUDA_TRY(cudaEventRecord(e0));
-    dmma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
+    for (int i = 0; i < kReps; ++i) dmma_peak_kernel<<<blocks, threads>>>(d, 0.999999, 1e-7);
     SHTB_CUDA_TRY(cudaEventRecord(e1));
     SHTB_CUDA_TRY(cudaEventSynchronize(e1));
     SHTB_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
     // each mma.sync m8n8k4 is 8*8*4 FMAs for the warp
     const double warps = (double)blocks * threads / 32.0;
-    *dmma = 2.0 * 256.0 * 4.0 * (kIters / 4) * warps / (ms * 1e-3) / 1e9;
+    *dmma = kReps * 2.0 * 256.0 * 4.0 * (kIters / 4) * warps / (ms * 1e-3) / 1e9;
 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
