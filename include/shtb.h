@@ -212,6 +212,34 @@ int shtb_test_legendre_adjoint(shtb_plan plan, const double *q_dev, double *alm_
                                int nmaps, void *stream);
 
 /*
+ * Synthesis without any device allocation.  Same result and arguments as
+ * shtb_synthesize, but its scratch (the scaled a_lm and the q_m(z_k) work
+ * array) lives in one static device array of SHTB_NOALLOC_SCRATCH_BYTES
+ * instead of the plan's workspace.  This has no counterpart in the paper; it
+ * serves callers that cannot allocate device memory when they transform:
+ * processes whose device memory is already held by another allocator (a
+ * framework's caching pool or a preallocating runtime), and loops that must
+ * not pay for the implicit device synchronisation of cudaMalloc.  The plan
+ * itself is still created, and allocated, beforehand.
+ *  - Limit: 16 nmaps (L+1)(L+2)/2 bytes (rounded up to 256) plus
+ *    16 nmaps (4 nside - 1)(L+1) bytes must fit in SHTB_NOALLOC_SCRATCH_BYTES
+ *    (64 MiB), e.g. one map at nside = 512, L = 1024; larger requests return
+ *    SHTB_ENOTSUP and leave the output untouched.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (that device current) and caches it; make that
+ *    first call before any stream capture.  Every GPU that loads the library
+ *    holds the array until the process exits.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose work overlaps on the GPU (other streams, other threads)
+ *    race on it and must be ordered by the caller.  No state is carried from
+ *    call to call: every scratch entry is written before it is read.
+ * Errors: SHTB_EINVAL, SHTB_EMISMATCH, SHTB_ENOTSUP, SHTB_ECUDA.
+ */
+#define SHTB_NOALLOC_SCRATCH_BYTES (64u << 20)
+int shtb_synthesize_noalloc(shtb_plan plan, const double *alm_dev, double *map_dev, int nmaps,
+                            void *stream);
+
+/*
  * Host-only check of the plan tables (needs no GPU): Ptilde_l^m(z_r) for
  * l = m..lmax at HEALPix half-ring r (0-based from the north pole, r < 2 nside),
  * evaluated on the CPU with the same per-(l, m) constants, start values and

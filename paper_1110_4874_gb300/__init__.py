@@ -89,6 +89,7 @@ SIGNATURES = {
     "shtb_test_phi_adjoint": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_legendre_adjoint": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_host_recurrence": (_I, [_I, _I, _I, _I, _DP]),
+    "shtb_synthesize_noalloc": (_I, [_P, _P, _P, _I, _P]),
 }
 
 _lib = None
@@ -195,6 +196,14 @@ def _call_dev(name, plan, src, src_dtype, dst, dst_dtype, nmaps, stream):
 def shtb_synthesize(plan, alm, maps, nmaps: int, stream=None) -> None:
     import torch
     _call_dev("shtb_synthesize", plan, alm, torch.complex128, maps, torch.float64, nmaps, stream)
+
+
+def shtb_synthesize_noalloc(plan, alm, maps, nmaps: int, stream=None) -> None:
+    """shtb_synthesize with its scratch in the library's static device array
+    (no device allocation by the call; size-limited, see include/shtb.h)."""
+    import torch
+    _call_dev("shtb_synthesize_noalloc", plan, alm, torch.complex128, maps, torch.float64, nmaps,
+              stream)
 
 
 def shtb_adjoint(plan, maps, alm, nmaps: int, stream=None) -> None:
