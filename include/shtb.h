@@ -108,8 +108,12 @@ int shtb_plan_opts_init(shtb_plan_opts *opts);
  * values past the 1e-30 crop (Appendix, "Efficient code for Legendre
  * transforms"), the ring phase/FFT tables of Eq. (tau), and, when eps > 0,
  * the butterfly-compressed operator of Sec. 3.2 at ID tolerance eps
- * (Eq. ID-approximation).  eps <= 0 gives the uncompressed transform (the
- * "zero levels of compression" limit of Sec. 3.3).
+ * (Eq. ID-approximation), with eps the relative tolerance of every ID (each
+ * block's truncated pivoted QR stops once the largest remaining column norm
+ * is at most eps times the block's first pivot).  eps <= 0 gives the
+ * uncompressed transform (the "zero levels of compression" limit of
+ * Sec. 3.3).  The adjoint of a compressed plan currently evaluates the
+ * uncompressed operator.
  * nside >= 1, 0 <= lmax <= 8192; opts may be NULL.  On success *out holds a
  * plan that owns all its device memory; release it with shtb_plan_destroy.
  * Errors: SHTB_EINVAL, SHTB_ENOTSUP, SHTB_ENOMEM, SHTB_ECUDA.
@@ -212,8 +216,10 @@ int shtb_test_legendre_adjoint(shtb_plan plan, const double *q_dev, double *alm_
                                int nmaps, void *stream);
 
 /*
- * Synthesis without any device allocation.  Same result and arguments as
- * shtb_synthesize, but its scratch (the scaled a_lm and the q_m(z_k) work
+ * Synthesis without any device allocation.  Same arguments as
+ * shtb_synthesize and, for uncompressed plans (eps <= 0), the same maps bit
+ * for bit; for compressed plans it evaluates the uncompressed operator,
+ * which agrees with shtb_synthesize to within the plan's tolerance.  Its scratch (the scaled a_lm and the q_m(z_k) work
  * array) lives in one static device array of SHTB_NOALLOC_SCRATCH_BYTES
  * instead of the plan's workspace.  This has no counterpart in the paper; it
  * serves callers that cannot allocate device memory when they transform:
@@ -247,6 +253,30 @@ int shtb_synthesize_noalloc(shtb_plan plan, const double *alm_dev, double *map_d
  * out: lmax - m + 1 doubles (host).  Errors: SHTB_EINVAL.
  */
 int shtb_test_host_recurrence(int nside, int lmax, int m, int r, double *out);
+
+/*
+ * Host-only check of the interpolative decomposition (Sec. 3.1, Eq. ID) used
+ * by the butterfly compression: for the rows x n column-major block A and
+ * relative tolerance eps, writes the rank k, the k skeleton column indices
+ * (skel_out, n slots) and the full k x n interpolation matrix (T_out, n*n
+ * slots, row-major; identity on the skeleton, 0 on all-zero columns) such
+ * that A ~= A[:, skel] * T.  Errors: SHTB_EINVAL.
+ */
+int shtb_test_host_id(int rows, int n, const double *A, double eps, int *k_out, int *skel_out,
+                      double *T_out);
+
+/*
+ * Host-only check of the butterfly compression (Sec. 3.2) of one Legendre
+ * matrix Lambda^{m,t} (rows l = m+t+2j, columns the HEALPix rings with
+ * z >= 0): builds the compressed operator exactly as shtb_plan_create does
+ * and applies it on the CPU, the way the device kernels do, to the real
+ * vector a (chain_len = floor((lmax-m-t)/2)+1 entries).  q_out (2 nside
+ * doubles) receives the compressed Lambda^T a, q_exact the dense product;
+ * info[0..3] = {depth, dense interpolation elements, stored residual
+ * elements, identity entries}.  Errors: SHTB_EINVAL.
+ */
+int shtb_test_host_butterfly(int nside, int lmax, double eps, int m, int t, int leaf_cols,
+                             const double *a, double *q_out, double *q_exact, long long *info);
 
 #ifdef __cplusplus
 }

@@ -90,6 +90,9 @@ SIGNATURES = {
     "shtb_test_legendre_adjoint": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_host_recurrence": (_I, [_I, _I, _I, _I, _DP]),
     "shtb_synthesize_noalloc": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_test_host_id": (_I, [_I, _I, _DP, _D, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
+    "shtb_test_host_butterfly": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
+                                      ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _lib = None
@@ -279,6 +282,37 @@ def shtb_test_host_recurrence(nside: int, lmax: int, m: int, r: int):
     _check(lib().shtb_test_host_recurrence(nside, lmax, m, r, out.ctypes.data_as(_DP)),
            "shtb_test_host_recurrence")
     return out
+
+
+def shtb_test_host_id(A, eps: float):
+    """ID of a real matrix A (rows x n): returns (k, skel, T) with A ~= A[:, skel] @ T."""
+    import numpy as np
+    A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    rows, n = A.shape
+    k = ctypes.c_int()
+    skel = np.zeros(max(n, 1), dtype=np.int32)
+    T = np.zeros(max(n * n, 1))
+    _check(lib().shtb_test_host_id(rows, n, A.ctypes.data_as(_DP), float(eps), ctypes.byref(k),
+                                   skel.ctypes.data_as(ctypes.POINTER(_I)), T.ctypes.data_as(_DP)),
+           "shtb_test_host_id")
+    kk = k.value
+    return kk, skel[:kk].copy(), T[:kk * n].reshape(kk, n).copy()
+
+
+def shtb_test_host_butterfly(nside: int, lmax: int, eps: float, m: int, t: int, a,
+                             leaf_cols: int = 32):
+    """Compressed and dense Lambda^T a for one (m, parity) on the host."""
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    Z = 2 * nside
+    q = np.zeros(Z)
+    qe = np.zeros(Z)
+    info = (ctypes.c_longlong * 4)()
+    _check(lib().shtb_test_host_butterfly(nside, lmax, float(eps), m, t, leaf_cols,
+                                          a.ctypes.data_as(_DP), q.ctypes.data_as(_DP),
+                                          qe.ctypes.data_as(_DP), info),
+           "shtb_test_host_butterfly")
+    return q, qe, {"depth": info[0], "n_dense": info[1], "n_r": info[2], "n_ident": info[3]}
 
 
 # ------------------------------------------------------------ convenience

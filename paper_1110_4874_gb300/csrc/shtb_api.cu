@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 
+#include "shtb_butterfly.h"
 #include "shtb_internal.h"
 
 namespace {
@@ -27,6 +28,8 @@ struct Workspace {
     // host-buffer variants
     double2 *alm = nullptr;     // [nmaps][nalm]
     double *map = nullptr;      // [nmaps][npix]
+    // butterfly apply (compressed plans): two u buffers and q^t
+    void *bf = nullptr;
 };
 
 size_t q_bytes(const shtb_plan_s *p, int nmaps)
@@ -46,7 +49,7 @@ size_t ws_total(const shtb_plan_s *p, int nmaps)
 {
     return align256(alm_bytes(p, nmaps)) * 2 + align256(q_bytes(p, nmaps)) +
            align256(adj_bytes(p, nmaps)) + align256(alm_bytes(p, nmaps)) +
-           align256(sizeof(double) * (size_t)nmaps * p->npix);
+           align256(sizeof(double) * (size_t)nmaps * p->npix) + align256(bf_workspace_bytes(p));
 }
 
 Workspace carve(shtb_plan_s *p, int nmaps)
@@ -58,7 +61,8 @@ Workspace carve(shtb_plan_s *p, int nmaps)
     w.adj = c;              c += align256(adj_bytes(p, nmaps));
     w.aacc = (double2 *)c;  c += align256(alm_bytes(p, nmaps));
     w.alm = (double2 *)c;   c += align256(alm_bytes(p, nmaps));
-    w.map = (double *)c;
+    w.map = (double *)c;    c += align256(sizeof(double) * (size_t)nmaps * p->npix);
+    w.bf = c;
     return w;
 }
 
@@ -125,11 +129,15 @@ int run_synthesis(shtb_plan_s *p, const double2 *alm, double *map, int nmaps, cu
     int rc = ensure_ws(p, nmaps);
     if (rc) return rc;
     Workspace w = carve(p, nmaps);
-    {
-        StageTimer t(p, st, 4);
-        if ((rc = launch_alm_prescale(p, alm, w.ap, nmaps, st))) return rc;
-    }
-    {
+    if (p->bf) {
+        // compressed operator (Sec. 3.2): residual blocks, butterfly levels, parity combine
+        StageTimer t(p, st, 0);
+        if ((rc = launch_bf_synth(p, alm, w.ap, w.bf, w.q, nmaps, st))) return rc;
+    } else {
+        {
+            StageTimer t(p, st, 4);
+            if ((rc = launch_alm_prescale(p, alm, w.ap, nmaps, st))) return rc;
+        }
         StageTimer t(p, st, 0);
         if ((rc = launch_legendre_synth(p, w.ap, w.q, nmaps, st))) return rc;
     }
@@ -208,7 +216,6 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
     if (!(eps == eps) || eps > 1.0) return shtb_fail(SHTB_EINVAL, "eps must be a number <= 1");
     if (lmax > 8192) return shtb_fail(SHTB_ENOTSUP, "lmax > 8192");
     if (nside > 2048) return shtb_fail(SHTB_ENOTSUP, "nside > 2048");
-    if (eps > 0.0) return shtb_fail(SHTB_ENOTSUP, "compressed plans (eps > 0) are not available in this build");
     auto t0 = std::chrono::steady_clock::now();
     shtb_plan_s *p = new (std::nothrow) shtb_plan_s();
     if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
@@ -231,6 +238,7 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
     }
     p->device = dev;
     int rc = shtb_build_dense_plan(p);
+    if (rc == SHTB_OK && eps > 0.0) rc = shtb_build_butterfly(p);
     if (rc) {
         shtb_plan_destroy(p);
         return rc;
@@ -241,8 +249,10 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
     p->stats.nrings = p->nrings;
     p->stats.npix = p->npix;
     p->stats.nalm = p->nalm;
-    p->stats.compressed = 0;
-    p->stats.depth_hist[0] = 2 * (lmax + 1);
+    if (!p->bf) {
+        p->stats.compressed = 0;
+        p->stats.depth_hist[0] = 2 * (lmax + 1);
+    }
     p->stats.build_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
@@ -258,6 +268,7 @@ int shtb_plan_destroy(shtb_plan p)
     for (void *a : p->allocations) cudaFree(a);
     if (p->ws) cudaFree(p->ws);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    bf_release(p);
     if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
     delete p;
     return SHTB_OK;

@@ -1,0 +1,225 @@
+// Kernel (a): application of the butterfly-compressed Legendre operator
+// (Sec. 3.2, Eq. factor-into-block-diagonal) for synthesis, q^t = Lambda^T a,
+// level by level over all (m, parity) chains at once.
+//
+//   bf_r_kernel      u = R^T a_I for every residual block (top level of each
+//                    chain; depth-0 chains write q^t directly);
+//   bf_level_kernel  one item = two sibling nodes sharing a candidate list:
+//                    v = T_top^T u_top + T_bot^T u_bot, split into the parent
+//                    level's two u vectors (or q^t on a leaf block at level 1);
+//                    identity part = adds, dense part = k x nd dot products
+//                    (Appendix: the identity-embedded interpolation matrices);
+//   bf_combine_kernel q_m(+z) = q^0 + q^1, q_m(-z) = q^0 - q^1 (Eq. q-even-odd2)
+//                    into the ring-major q of the ring stage.
+// One warp per work item; all maps of a group (up to 8, 2 real components
+// each) are carried per entry so every stored matrix element is read once
+// per group and used for 2 x maps FMAs.  All stages are FP64-bound on GB300.
+#include <cuda_runtime.h>
+
+#include "shtb_butterfly.h"
+
+namespace {
+
+constexpr int kBfWarps = 4;
+
+__device__ __forceinline__ long long dalm_off(int L, int m)
+{
+    return (long long)m * (2 * L + 1 - m) / 2 + m;
+}
+
+// ai[idx][b] = a_lm[b][idx] for the group's maps (Im a_l0 = 0, Sec. 2.1)
+__global__ void bf_interleave_kernel(PlanView v, const double2 *__restrict__ alm,
+                                     double2 *__restrict__ ai, int nmaps)
+{
+    const int m = blockIdx.x;
+    const int L = v.lmax;
+    const long long off = dalm_off(L, m);
+    const int n = L - m + 1;
+    for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {
+        const int b = i / n, dl = i - b * n;
+        const long long idx = off + dl;
+        const double2 a = alm[(size_t)b * v.nalm + idx];
+        ai[(size_t)idx * nmaps + b] = make_double2(a.x, m == 0 ? 0.0 : a.y);
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32 * kBfWarps)
+bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int *__restrict__ ints,
+            const double *__restrict__ dbl, const double2 *__restrict__ ai, int nmaps, int b0,
+            double *__restrict__ ubuf0, double *__restrict__ ubuf1, const int *__restrict__ depth_par,
+            double *__restrict__ qt)
+{
+    constexpr int C = 2 * NB;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kBfWarps + (threadIdx.x >> 5);
+    if (w >= nitems) return;
+    const BfRItem it = items[w];
+    const double *__restrict__ R = dbl + it.data_off;
+    const long long aoff = dalm_off(v.lmax, it.m) + it.t;   // chain row j at aoff + 2j
+    double *ubuf = depth_par[it.m * 2 + it.t] ? ubuf1 : ubuf0;
+    for (int s = lane; s < it.k; s += 32) {
+        double acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        for (int j = 0; j < it.nrows; ++j) {
+            const double r = R[(size_t)j * it.k + s];
+            const double2 *aj = ai + (size_t)(aoff + 2 * (it.j0 + j)) * nmaps + b0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const double2 a = __ldg(aj + b);
+                acc[2 * b] = fma(r, a.x, acc[2 * b]);
+                acc[2 * b + 1] = fma(r, a.y, acc[2 * b + 1]);
+            }
+        }
+        double *dst = it.to_rings ? qt + (size_t)ints[it.out_off + s] * C
+                                  : ubuf + (size_t)(it.out_off + s) * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) dst[c] = acc[c];
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32 * kBfWarps)
+bf_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__restrict__ ints,
+                const double *__restrict__ dbl, const double *__restrict__ uin,
+                double *__restrict__ uout, double *__restrict__ qt)
+{
+    constexpr int C = 2 * NB;
+    extern __shared__ double sout[];     // [kBfWarps][kMaxCand * C]
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int w = blockIdx.x * kBfWarps + wib;
+    if (w >= nitems) return;
+    const BfItem it = items[w];
+    double *out = sout + (size_t)wib * shtb::kMaxCand * C;
+    for (int i = lane; i < it.nc * C; i += 32) out[i] = 0.0;
+    __syncwarp();
+    for (int s = 0; s < 2; ++s) {
+        const int k = it.k[s], nd = it.nd[s];
+        const double *__restrict__ u = uin + (size_t)it.u_off[s] * C;
+        const double *__restrict__ T = dbl + it.T_off[s];
+        const int *__restrict__ dpos = ints + it.dpos_off[s];
+        for (int d = lane; d < nd; d += 32) {
+            double acc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = 0.0;
+            for (int i = 0; i < k; ++i) {
+                const double t = T[(size_t)i * nd + d];
+                const double *ui = u + (size_t)i * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] = fma(t, __ldg(ui + c), acc[c]);
+            }
+            double *o = out + dpos[d] * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) o[c] += acc[c];
+        }
+        const int *__restrict__ ipos = ints + it.ipos_off[s];
+        for (int i = lane; i < k; i += 32) {
+            double *o = out + ipos[i] * C;
+            const double *ui = u + (size_t)i * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) o[c] += __ldg(ui + c);
+        }
+        __syncwarp();
+    }
+    if (it.to_rings) {
+        const int *__restrict__ ent = ints + it.out_off;
+        for (int i = lane; i < it.nc * C; i += 32) {
+            const int cpos = i / C, c = i - cpos * C;
+            qt[(size_t)ent[cpos] * C + c] = out[i];
+        }
+    } else {
+        double *dst = uout + (size_t)it.out_off * C;
+        for (int i = lane; i < it.nc * C; i += 32) dst[i] = out[i];
+    }
+}
+
+// q[b0+b][ring][m]: north ring r gets q^0 + q^1, its mirror q^0 - q^1
+template <int NB>
+__global__ void bf_combine_kernel(PlanView v, const double *__restrict__ qt, double2 *__restrict__ q,
+                                  int b0)
+{
+    constexpr int C = 2 * NB;
+    const int m = blockIdx.x;
+    const int L = v.lmax, Z = v.nhalf;
+    const bool odd = m + 1 <= L;    // chain t = 1 exists
+    for (int r = threadIdx.x; r < Z; r += blockDim.x) {
+        const double *e0 = qt + ((size_t)(m * 2 + 0) * Z + r) * C;
+        const double *e1 = qt + ((size_t)(m * 2 + 1) * Z + r) * C;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const double2 x0 = make_double2(e0[2 * b], e0[2 * b + 1]);
+            const double2 x1 = odd ? make_double2(e1[2 * b], e1[2 * b + 1]) : make_double2(0.0, 0.0);
+            double2 *qb = q + (size_t)(b0 + b) * v.nrings * (L + 1);
+            qb[(size_t)r * (L + 1) + m] = make_double2(x0.x + x1.x, x0.y + x1.y);
+            if (r < Z - 1)
+                qb[(size_t)(v.nrings - 1 - r) * (L + 1) + m] = make_double2(x0.x - x1.x, x0.y - x1.y);
+        }
+    }
+}
+
+template <int NB>
+int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
+              double *qt, double2 *q, cudaStream_t st)
+{
+    const BfPlanDev &bf = *p->bf;
+    const PlanView &v = p->view;
+    if (bf.n_ritems > 0) {
+        const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
+        bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(v, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
+                                                        nmaps, b0, u0, u1, bf.depth_parity, qt);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    for (int lev = bf.depth_max; lev >= 1; --lev) {
+        const int n = bf.level_counts[lev - 1];
+        if (n == 0) continue;
+        double *uin = (lev % 2) ? u1 : u0;
+        double *uout = ((lev - 1) % 2) ? u1 : u0;
+        const unsigned grid = (unsigned)((n + kBfWarps - 1) / kBfWarps);
+        const size_t smem = sizeof(double) * kBfWarps * shtb::kMaxCand * 2 * NB;
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(bf_level_kernel<NB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bf_level_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, bf.ints,
+                                                               bf.dbl, uin, uout, qt);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    bf_combine_kernel<NB><<<p->lmax + 1, 256, 0, st>>>(v, qt, q, b0);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    return SHTB_OK;
+}
+
+}  // namespace
+
+size_t bf_workspace_bytes(const shtb_plan_s *p)
+{
+    if (!p->bf) return 0;
+    const size_t entry = sizeof(double) * 16;   // up to 8 maps x (re, im) per group
+    return (2 * (size_t)p->bf->u_entries + (size_t)p->bf->qt_entries) * entry + 512;
+}
+
+int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double2 *q,
+                    int nmaps, cudaStream_t st)
+{
+    const BfPlanDev &bf = *p->bf;
+    const size_t entry = 16;
+    double *u0 = (double *)ws;
+    double *u1 = u0 + (size_t)bf.u_entries * entry;
+    double *qt = u1 + (size_t)bf.u_entries * entry;
+    bf_interleave_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ai, nmaps);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    for (int b0 = 0; b0 < nmaps;) {
+        const int left = nmaps - b0;
+        int rc;
+        if (left >= 8) { rc = run_group<8>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 8; }
+        else if (left >= 4) { rc = run_group<4>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 4; }
+        else if (left >= 2) { rc = run_group<2>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 2; }
+        else { rc = run_group<1>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 1; }
+        if (rc) return rc;
+    }
+    return SHTB_OK;
+}

@@ -76,6 +76,8 @@ struct PlanView {
     int Wlen;
 };
 
+struct BfPlanDev;
+
 struct shtb_plan_s {
     int nside = 0, lmax = 0;
     double eps = 0;
@@ -96,6 +98,9 @@ struct shtb_plan_s {
     // device allocations owned by the plan (freed in destroy)
     std::vector<void *> allocations;
     PlanView view{};
+
+    // butterfly-compressed operator (eps > 0), owned
+    BfPlanDev *bf = nullptr;
 
     // workspace (grown on demand)
     void *ws = nullptr;
@@ -138,6 +143,12 @@ int launch_phi_synth(const shtb_plan_s *p, const double2 *q, double *map, int nm
                      cudaStream_t st);
 int launch_phi_adjoint(const shtb_plan_s *p, const double *map, double2 *q, int nmaps,
                        cudaStream_t st);
+
+// shtb_butterfly.cu
+size_t bf_workspace_bytes(const shtb_plan_s *p);
+int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double2 *q,
+                    int nmaps, cudaStream_t st);
+void bf_release(shtb_plan_s *p);
 
 // shtb_util.cu
 int measure_fp64_peak(int device, double *dfma, double *dmma);

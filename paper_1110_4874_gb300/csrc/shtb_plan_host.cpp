@@ -15,34 +15,138 @@
 
 #include "shtb_dd.h"
 #include "shtb_internal.h"
+#include "shtb_plan_detail.h"
 
 using shtb::DD;
 using shtb::dd;
+using shtb::HalfRing;
+using shtb::kCrop;
+using shtb::parallel_for;
+
+
+// ------------------------------------------------------------ shared helpers
+namespace shtb {
+
+HalfRing half_ring(long long N, long long i)
+{
+    long long zn, zd, sn, sd, en;
+    if (i < N) {
+        zn = 3 * N * N - i * i;
+        zd = 3 * N * N;
+        sn = i * i * (6 * N * N - i * i);
+        sd = 9 * N * N * N * N;
+        en = i * i;                 // 1 - z = i^2 / (3N^2)
+    } else {
+        zn = 4 * N - 2 * i;
+        zd = 3 * N;
+        sn = (2 * i - N) * (7 * N - 2 * i);
+        sd = 9 * N * N;
+        en = 2 * i - N;             // 1 - z = (2i - N) / (3N)
+    }
+    HalfRing h;
+    DD zq = dd((double)zn) / dd((double)zd);
+    h.z = to_double(zq);
+    h.z2 = to_double(ddmul((double)zn, (double)zn) / ddmul((double)zd, (double)zd));
+    DD s2 = dd((double)sn) / dd((double)sd);
+    h.s2 = to_double(s2);
+    h.eps1 = to_double(dd((double)en) / dd((double)zd));
+    h.sdd = sqrt(s2);
+    return h;
+}
+
+// c_m = sqrt(1/(4 pi) prod_{i=1}^m (2i+1)/(2i)) as dd, m = 0..L
+std::vector<DD> diag_norms(int L)
+{
+    std::vector<DD> out(L + 1);
+    DD c2 = dd(1.0) / (DD{shtb::kPiHi, shtb::kPiLo} * 4.0);
+    out[0] = shtb::sqrt(c2);
+    for (int i = 1; i <= L; ++i) {
+        c2 = c2 * (dd(2.0 * i + 1.0) / dd(2.0 * i));
+        out[i] = shtb::sqrt(c2);
+    }
+    return out;
+}
+
+// x^m as (mantissa dd in [0.5,1), exponent) by binary powering
+DD dd_pow(DD x, int m, int *E)
+{
+    auto norm = [](DD v, int *e) {
+        int k;
+        std::frexp(v.hi, &k);
+        *e += k;
+        return DD{std::ldexp(v.hi, -k), std::ldexp(v.lo, -k)};
+    };
+    DD r = dd(1.0), b = x;
+    int er = 0, eb = 0;
+    b = norm(b, &eb);
+    while (m > 0) {
+        if (m & 1) { r = r * b; er += eb; r = norm(r, &er); }
+        m >>= 1;
+        if (m) { b = b * b; eb *= 2; b = norm(b, &eb); }
+    }
+    *E = er;
+    return r;
+}
+
+// b_l = sqrt((l^2 - m^2)/(4 l^2 - 1)) for l = m+1..L (index l - m) of the
+// textbook one-step recurrence Ptilde_l = (z Ptilde_{l-1} - b_{l-1} Ptilde_{l-2}) / b_l
+std::vector<double> one_step_coefs(int L, int m)
+{
+    std::vector<double> b(L - m + 2, 0.0);
+    for (int l = m + 1; l <= L; ++l)
+        b[l - m] = std::sqrt(((double)(l - m) * (double)(l + m)) /
+                             ((double)(2 * l - 1) * (double)(2 * l + 1)));
+    return b;
+}
+
+
+void legendre_column(int L, int m, const HalfRing &h, DD cm, const std::vector<double> &b,
+                     double *out)
+{
+    const double sq = std::sqrt(2.0 * m + 3.0);
+    const bool near_pole = h.z > 0.5;
+    auto zmul = [&](double v) { return near_pole ? v - h.eps1 * v : h.z * v; };
+    int E = 0;
+    DD pm = dd_pow(h.sdd, m, &E) * cm;
+    double P0 = to_double(pm);
+    if (m & 1) P0 = -P0;
+    auto emit = [&](int l, double Pm) {
+        const double v = E == 0 ? Pm : std::ldexp(Pm, E);
+        out[l - m] = std::fabs(v) >= kCrop ? v : 0.0;
+    };
+    emit(m, P0);
+    if (m == L) return;
+    double P1 = sq * zmul(P0);
+    emit(m + 1, P1);
+    for (int l = m + 2; l <= L; ++l) {
+        double P2 = (zmul(P1) - b[l - 1 - m] * P0) / b[l - m];
+        P0 = P1;
+        P1 = P2;
+        if (E != 0 && P1 != 0.0) {
+            int k;
+            std::frexp(P1, &k);
+            if (k + E > -900) {
+                P0 = std::ldexp(P0, E);
+                P1 = std::ldexp(P1, E);
+                E = 0;
+            } else if (k > 600) {
+                P0 = std::ldexp(P0, -512);
+                P1 = std::ldexp(P1, -512);
+                E += 512;
+            }
+        }
+        emit(l, P1);
+    }
+}
+
+}  // namespace shtb
+
+using shtb::diag_norms;
+using shtb::dd_pow;
+using shtb::half_ring;
+using shtb::one_step_coefs;
 
 namespace {
-
-// ------------------------------------------------------------ threading
-template <class F>
-void parallel_for(int n, int nthreads, F &&fn)
-{
-    if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
-    nthreads = std::min(nthreads, std::max(n, 1));
-    std::atomic<int> next{0};
-    auto worker = [&]() {
-        for (;;) {
-            int i = next.fetch_add(1);
-            if (i >= n) break;
-            fn(i);
-        }
-    };
-    if (nthreads == 1) {
-        worker();
-        return;
-    }
-    std::vector<std::thread> th;
-    for (int t = 0; t < nthreads; ++t) th.emplace_back(worker);
-    for (auto &t : th) t.join();
-}
 
 // -------------------------------------------- cos/sin of rational angles
 // (cos, sin)(pi * num / den) with the angle folded by integer symmetries
@@ -93,48 +197,6 @@ void dif_forward(std::vector<std::complex<double>> &x, const std::vector<std::co
             }
         }
     }
-}
-
-// ------------------------------------------------------------- geometry
-struct HalfRing {
-    double z;        // cos(theta), correctly rounded
-    double z2;       // z^2, correctly rounded from the exact ratio
-    double s2;       // sin^2(theta), correctly rounded from the exact ratio
-    double eps1;     // 1 - z, correctly rounded from the exact ratio
-    DD sdd;          // sin(theta) as dd
-};
-
-// Ring r (0-based, north to south) of the HEALPix RING grid: i = r + 1 is
-// the ring number counted from the north pole, mirrored in the south.
-//   polar i < N : z = 1 - i^2/(3N^2), J = 4i, phi_j = pi (2j + 1) / J
-//   belt        : z = (4N - 2i)/(3N), J = 4N, phi_j = pi (2j + s) / J,
-//                 s = 1 iff (i + N) is even
-HalfRing half_ring(long long N, long long i)
-{
-    long long zn, zd, sn, sd, en;
-    if (i < N) {
-        zn = 3 * N * N - i * i;
-        zd = 3 * N * N;
-        sn = i * i * (6 * N * N - i * i);
-        sd = 9 * N * N * N * N;
-        en = i * i;                 // 1 - z = i^2 / (3N^2)
-    } else {
-        zn = 4 * N - 2 * i;
-        zd = 3 * N;
-        sn = (2 * i - N) * (7 * N - 2 * i);
-        sd = 9 * N * N;
-        en = 2 * i - N;             // 1 - z = (2i - N) / (3N)
-    }
-    HalfRing h;
-    DD zq = dd((double)zn) / dd((double)zd);
-    h.z = shtb::to_double(zq);
-    h.z2 = shtb::to_double(shtb::ddmul((double)zn, (double)zn) /
-                           shtb::ddmul((double)zd, (double)zd));
-    DD s2 = dd((double)sn) / dd((double)sd);
-    h.s2 = shtb::to_double(s2);
-    h.eps1 = shtb::to_double(dd((double)en) / dd((double)zd));
-    h.sdd = shtb::sqrt(s2);
-    return h;
 }
 
 // ------------------------------------------------ recurrence constants
@@ -194,52 +256,6 @@ void build_coefficients(int L, int m, RecCoef *out /* indexed by l - m */)
     }
 }
 
-// c_m = sqrt(1/(4 pi) prod_{i=1}^m (2i+1)/(2i)) as dd, m = 0..L
-std::vector<DD> diag_norms(int L)
-{
-    std::vector<DD> out(L + 1);
-    DD c2 = dd(1.0) / (DD{shtb::kPiHi, shtb::kPiLo} * 4.0);
-    out[0] = shtb::sqrt(c2);
-    for (int i = 1; i <= L; ++i) {
-        c2 = c2 * (dd(2.0 * i + 1.0) / dd(2.0 * i));
-        out[i] = shtb::sqrt(c2);
-    }
-    return out;
-}
-
-// x^m as (mantissa dd in [0.5,1), exponent) by binary powering
-DD dd_pow(DD x, int m, int *E)
-{
-    auto norm = [](DD v, int *e) {
-        int k;
-        std::frexp(v.hi, &k);
-        *e += k;
-        return DD{std::ldexp(v.hi, -k), std::ldexp(v.lo, -k)};
-    };
-    DD r = dd(1.0), b = x;
-    int er = 0, eb = 0;
-    b = norm(b, &eb);
-    while (m > 0) {
-        if (m & 1) { r = r * b; er += eb; r = norm(r, &er); }
-        m >>= 1;
-        if (m) { b = b * b; eb *= 2; b = norm(b, &eb); }
-    }
-    *E = er;
-    return r;
-}
-
-constexpr double kCrop = 1e-30;   // Appendix: values below 1e-30 are neglected
-
-// b_l = sqrt((l^2 - m^2)/(4 l^2 - 1)) for l = m+1..L (index l - m) of the
-// textbook one-step recurrence Ptilde_l = (z Ptilde_{l-1} - b_{l-1} Ptilde_{l-2}) / b_l
-std::vector<double> one_step_coefs(int L, int m)
-{
-    std::vector<double> b(L - m + 2, 0.0);
-    for (int l = m + 1; l <= L; ++l)
-        b[l - m] = std::sqrt(((double)(l - m) * (double)(l + m)) /
-                             ((double)(2 * l - 1) * (double)(2 * l + 1)));
-    return b;
-}
 
 // For order m at one half-ring: per parity t the first chain index js[t]
 // with |Ptilde_{m+t+2j}^m| >= 1e-30 and the rescaled values V = Ptilde/sigma

@@ -1,0 +1,88 @@
+"""Host-side (no GPU) checks of the butterfly compression: the interpolative
+decomposition against the guarantees of Sec. 3.1 (Eq. ID, Eq. ID-approximation),
+and the compressed operator of Sec. 3.2 applied on the CPU against the dense
+Legendre matrix built independently from the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1110_4874_gb300 as sh
+
+
+def test_id_exact_for_low_rank():
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((60, 7)) @ rng.standard_normal((7, 25))
+    k, skel, T = sh.shtb_test_host_id(A, 1e-13)
+    assert k == 7
+    np.testing.assert_array_equal(T[:, skel], np.eye(k))          # identity on the skeleton
+    assert np.abs(A - A[:, skel] @ T).max() < 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-10, 1e-13])
+def test_id_error_bound_on_legendre_blocks(eps):
+    """||A - A[:, skel] T|| <= sqrt(4k(n-k)+1) sigma_{k+1} (Eq. ID-approximation)
+    up to the truncation level, on blocks of the Legendre matrix."""
+    nside, lmax = 256, 512
+    rings = oracle.healpix_rings(nside)
+    for m, rows, cols in [(0, (100, 356), (30, 94)), (200, (0, 120), (300, 364)),
+                          (10, (256, 512), (0, 64))]:
+        ls = np.arange(m, lmax + 1)[rows[0]:rows[1]]
+        A = np.array([oracle.legendre(m, lmax, rings.z[c], rings.sinth[c], rings.zlo[c],
+                                      rings.sinlo[c])[ls - m] for c in range(*cols)]).T
+        k, skel, T = sh.shtb_test_host_id(A, eps)
+        n = A.shape[1]
+        s = np.linalg.svd(A, compute_uv=False)
+        err = np.linalg.norm(A - A[:, skel] @ T, 2)
+        bound = math.sqrt(4 * k * (n - k) + 1) * (s[k] if k < len(s) else 0.0)
+        assert err <= max(bound, 0.0) + 4 * eps * s[0] * math.sqrt(n)
+        assert err <= 4 * eps * s[0] * math.sqrt(n)
+        # the truncated QR keeps the interpolation coefficients modest
+        assert np.abs(T).max() < 50
+        assert k <= min(A.shape)
+
+
+def test_id_zero_and_empty_blocks():
+    k, skel, T = sh.shtb_test_host_id(np.zeros((10, 5)), 1e-10)
+    assert k == 0
+    A = np.zeros((8, 4))
+    A[:, 2] = np.arange(8)
+    k, skel, T = sh.shtb_test_host_id(A, 1e-10)
+    assert k == 1 and skel[0] == 2
+    np.testing.assert_array_equal(T, [[0, 0, 1, 0]])
+
+
+@pytest.mark.parametrize("nside,lmax,eps", [(128, 256, 1e-10), (256, 512, 1e-12),
+                                            (512, 1024, 1e-8), (64, 200, 1e-10)])
+def test_compressed_operator_matches_dense(nside, lmax, eps):
+    rng = np.random.default_rng(nside)
+    for m in [0, 1, lmax // 3, lmax // 2, lmax - 5, lmax]:
+        for t in (0, 1):
+            n = (lmax - m - t) // 2 + 1 if m + t <= lmax else 0
+            if n == 0:
+                continue
+            a = rng.standard_normal(n) / (m + 2 * np.arange(n) + 1 + t)
+            q, qe, info = sh.shtb_test_host_butterfly(nside, lmax, eps, m, t, a)
+            # the dense product from the oracle's (independent) Legendre values
+            rings = oracle.healpix_rings(nside)
+            lam = np.array([oracle.legendre(m, lmax, rings.z[r], rings.sinth[r], rings.zlo[r],
+                                            rings.sinlo[r])[t::2][:n] for r in range(2 * nside)])
+            want = lam @ a
+            scale = np.linalg.norm(want)
+            assert np.linalg.norm(qe - want) <= 1e-12 * scale + 1e-300
+            assert np.linalg.norm(q - want) <= 100 * eps * scale + 1e-300
+            if info["depth"] > 0:
+                assert info["n_dense"] + info["n_r"] < n * 2 * nside
+
+
+def test_compression_shrinks_with_resolution():
+    """The rank property (Sec. 3.2): the stored fraction of the m = 0 matrix
+    falls as L grows at fixed eps."""
+    fracs = []
+    for nside, lmax in [(128, 256), (512, 1024), (1024, 2048)]:
+        n = lmax // 2 + 1
+        q, qe, info = sh.shtb_test_host_butterfly(nside, lmax, 1e-10, 0, 0, np.ones(n))
+        fracs.append((info["n_dense"] + info["n_r"] + info["n_ident"]) / (n * 2 * nside))
+    assert fracs[0] > fracs[1] > fracs[2]
+    assert fracs[2] < 0.35

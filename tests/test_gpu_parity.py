@@ -185,3 +185,76 @@ def test_error_paths(plans):
     with pytest.raises(sh.ShtbError) as e:
         sh.shtb_plan_create(8, 16, float("nan"))
     assert e.value.code == sh.SHTB_EINVAL
+
+
+# ------------------------------------------------------------ compressed plans
+COMPRESSED = [(32, 64, 1e-12), (128, 256, 1e-10), (64, 100, 1e-10), (13, 30, 1e-8),
+              (256, 512, 1e-12), (16, 48, 1e-6)]
+
+
+@pytest.mark.parametrize("nside,lmax,eps", COMPRESSED)
+def test_compressed_synthesis_vs_oracle(nside, lmax, eps):
+    """Butterfly-compressed synthesis (Sec. 3.2) within the tolerance rule:
+    <= 1e-10 relative RMS at eps = 1e-12, <= 100 eps otherwise."""
+    plan = sh.Plan(nside, lmax, eps)
+    st = plan.stats()
+    assert st["compressed"] == 1
+    rings = oracle.healpix_rings(nside)
+    a = synthetic.gaussian_alm(lmax, 3, seed=77)
+    want = oracle.synthesize(rings, lmax, a)
+    got = plan.synthesize(dev(a)).cpu().numpy()
+    tol = 1e-10 if eps <= 1e-12 else 100 * eps
+    for b in range(3):
+        assert rel_rms(want[b], got[b]) <= tol
+    plan.close()
+
+
+def test_compressed_batches_match_single_maps():
+    plan = sh.Plan(64, 128, 1e-10)
+    a = dev(synthetic.gaussian_alm(128, 11, seed=3))
+    batch = plan.synthesize(a)
+    for b in range(11):
+        assert torch.equal(batch[b], plan.synthesize(a[b:b + 1])[0])
+    plan.close()
+
+
+def test_compressed_stats_count_less_work_than_dense():
+    plan = sh.Plan(256, 512, 1e-10)
+    st = plan.stats()
+    dense = sh.Plan(256, 512, 0.0).stats()
+    assert st["n_dense"] + st["n_rstored"] > 0
+    assert st["legendre_flops_per_map"] < dense["legendre_flops_per_map"]
+    assert sum(st["depth_hist"]) == 2 * 513
+    plan.close()
+
+
+# ------------------------------------------------------------ differentiation
+def test_autograd_matches_central_differences():
+    """loss = 0.5 ||Y a - d||^2 (the data model of Eq. datamodel): the gradient
+    from torch.autograd, whose backward is the adjoint kernel, equals central
+    finite differences; the loss is quadratic, so central differences are exact
+    up to rounding."""
+    nside, lmax = 16, 32
+    plan = sh.Plan(nside, lmax, 0.0)
+    a_true = dev(synthetic.gaussian_alm(lmax, 1, seed=4100))[0]
+    a0 = dev(synthetic.gaussian_alm(lmax, 1, seed=4000))[0]
+    d = plan.synthesize(a_true) + 0.1 * dev(synthetic.gaussian_map(plan.npix, 1, seed=4200))[0]
+    a = a0.clone().requires_grad_(True)
+    loss = 0.5 * torch.sum((sh.synthesize(a, plan) - d) ** 2)
+    loss.backward()
+    g = a.grad.detach()
+    m0 = torch.tensor(synthetic.m_of_index(lmax) == 0, device="cuda")
+    assert torch.all(g.imag[m0] == 0)
+
+    def L(x):
+        return 0.5 * torch.sum((plan.synthesize(x) - d) ** 2).item()
+
+    rng = np.random.default_rng(5)
+    h = 1e-4 * torch.linalg.norm(a0).item()
+    for _ in range(4):
+        v = dev(rng.standard_normal(plan.nalm) + 1j * rng.standard_normal(plan.nalm))
+        v = torch.where(m0, v.real.to(v.dtype), v)
+        fd = (L(a0 + h * v) - L(a0 - h * v)) / (2 * h)
+        an = torch.sum(g.real * v.real + g.imag * v.imag).item()
+        assert an == pytest.approx(fd, rel=1e-9)
+    plan.close()
