@@ -112,8 +112,8 @@ int shtb_plan_opts_init(shtb_plan_opts *opts);
  * block's truncated pivoted QR stops once the largest remaining column norm
  * is at most eps times the block's first pivot).  eps <= 0 gives the
  * uncompressed transform (the "zero levels of compression" limit of
- * Sec. 3.3).  The adjoint of a compressed plan currently evaluates the
- * uncompressed operator.
+ * Sec. 3.3); the adjoint of a compressed plan applies the transposed
+ * compressed operator, so it is the exact transpose of that plan's synthesis.
  * nside >= 1, 0 <= lmax <= 8192; opts may be NULL.  On success *out holds a
  * plan that owns all its device memory; release it with shtb_plan_destroy.
  * Errors: SHTB_EINVAL, SHTB_ENOTSUP, SHTB_ENOMEM, SHTB_ECUDA.

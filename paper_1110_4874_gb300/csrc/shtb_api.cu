@@ -157,6 +157,14 @@ int run_adjoint(shtb_plan_s *p, const double *map, double2 *alm, int nmaps, cuda
         StageTimer t(p, st, 2);
         if ((rc = launch_phi_adjoint(p, map, w.q, nmaps, st))) return rc;
     }
+    if (p->bf) {
+        // transposed butterfly (compressed plans)
+        StageTimer t(p, st, 3);
+        double2 *g = (double2 *)w.adj;
+        if ((rc = launch_adjoint_parity(p, w.q, g, nmaps, st))) return rc;
+        if ((rc = launch_bf_adjoint(p, g, w.aacc, w.bf, alm, nmaps, st))) return rc;
+        return SHTB_OK;
+    }
     {
         StageTimer t(p, st, 3);
         if ((rc = launch_legendre_adjoint(p, w.q, w.aacc, nmaps, w.adj, st))) return rc;

@@ -192,6 +192,159 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
     return SHTB_OK;
 }
 
+
+// ------------------------------------------------------------------ adjoint
+// a^t = Lambda g^t: the transposed butterfly.  Level items run bottom-up:
+// item (parent P, group G) gathers its candidate vector (g on a leaf block at
+// level 1, else the u of level l-1) and applies both children's T:
+// u_s = [I | T_s] v  (identity entries copy, dense rows are k x nd dots).
+template <int NB>
+__global__ void __launch_bounds__(32 * kBfWarps)
+bf_adj_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__restrict__ ints,
+                    const double *__restrict__ dbl, const double *__restrict__ uin,
+                    const double2 *__restrict__ g, int nmaps, int b0, double *__restrict__ uout)
+{
+    constexpr int C = 2 * NB;
+    extern __shared__ double sin_[];     // [kBfWarps][kMaxCand * C]
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int w = blockIdx.x * kBfWarps + wib;
+    if (w >= nitems) return;
+    const BfItem it = items[w];
+    double *in = sin_ + (size_t)wib * shtb::kMaxCand * C;
+    if (it.to_rings) {
+        const int *__restrict__ ent = ints + it.out_off;
+        for (int i = lane; i < it.nc * NB; i += 32) {
+            const int cpos = i / NB, b = i - cpos * NB;
+            const double2 x = g[(size_t)ent[cpos] * nmaps + b0 + b];
+            in[cpos * C + 2 * b] = x.x;
+            in[cpos * C + 2 * b + 1] = x.y;
+        }
+    } else {
+        const double *src = uin + (size_t)it.out_off * C;
+        for (int i = lane; i < it.nc * C; i += 32) in[i] = src[i];
+    }
+    __syncwarp();
+    for (int s = 0; s < 2; ++s) {
+        const int k = it.k[s], nd = it.nd[s];
+        const double *__restrict__ T = dbl + it.T_off[s];
+        const int *__restrict__ dpos = ints + it.dpos_off[s];
+        const int *__restrict__ ipos = ints + it.ipos_off[s];
+        for (int i = lane; i < k; i += 32) {
+            double acc[C];
+            const double *xi = in + ipos[i] * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = xi[c];
+            const double *Ti = T + (size_t)i * nd;
+            for (int d = 0; d < nd; ++d) {
+                const double t = Ti[d];
+                const double *x = in + dpos[d] * C;
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] = fma(t, x[c], acc[c]);
+            }
+            double *dst = uout + (size_t)(it.u_off[s] + i) * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) dst[c] = acc[c];
+        }
+    }
+}
+
+// a rows of one (chain, row interval): a_j = sum over its residual blocks of
+// R[j, :] u  (lane = row; every row of the interval is written, zero when no
+// block reaches it)
+template <int NB>
+__global__ void __launch_bounds__(32 * kBfWarps)
+bf_adj_r_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
+                const BfRItem *__restrict__ ritems, const int *__restrict__ ints,
+                const double *__restrict__ dbl, const double *__restrict__ u0,
+                const double *__restrict__ u1, const int *__restrict__ depth_par,
+                const double2 *__restrict__ g, int nmaps, int b0, double2 *__restrict__ aacc)
+{
+    constexpr int C = 2 * NB;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kBfWarps + (threadIdx.x >> 5);
+    if (w >= ngroups) return;
+    const BfRGroup gr = groups[w];
+    const double *ubuf = depth_par[gr.m * 2 + gr.t] ? u1 : u0;
+    const long long aoff = dalm_off(v.lmax, gr.m) + gr.t;
+    for (int j = gr.r0 + lane; j < gr.r1; j += 32) {
+        double acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        for (int q = 0; q < gr.nblk; ++q) {
+            const BfRItem it = ritems[ints[gr.blk_off + q]];
+            if (j < it.j0 || j >= it.j0 + it.nrows) continue;
+            const double *Rj = dbl + it.data_off + (size_t)(j - it.j0) * it.k;
+            for (int s = 0; s < it.k; ++s) {
+                const double r = Rj[s];
+                if (it.to_rings) {
+                    const double2 *x = g + (size_t)ints[it.out_off + s] * nmaps + b0;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        const double2 xb = __ldg(x + b);
+                        acc[2 * b] = fma(r, xb.x, acc[2 * b]);
+                        acc[2 * b + 1] = fma(r, xb.y, acc[2 * b + 1]);
+                    }
+                } else {
+                    const double *x = ubuf + (size_t)(it.out_off + s) * C;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[c] = fma(r, __ldg(x + c), acc[c]);
+                }
+            }
+        }
+        double2 *dst = aacc + (size_t)(aoff + 2 * j) * nmaps + b0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) dst[b] = make_double2(acc[2 * b], acc[2 * b + 1]);
+    }
+}
+
+// alm[b][idx] = c_m aacc[idx][b] (c_0 = 1 with Im a_l0 = 0, c_m = 2)
+__global__ void bf_finish_kernel(PlanView v, const double2 *__restrict__ aacc,
+                                 double2 *__restrict__ alm, int nmaps)
+{
+    const int m = blockIdx.x;
+    const int L = v.lmax;
+    const long long off = dalm_off(L, m);
+    const int n = L - m + 1;
+    const double cm = m == 0 ? 1.0 : 2.0;
+    for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {
+        const int b = i / n, dl = i - b * n;
+        const long long idx = off + dl;
+        const double2 a = aacc[(size_t)idx * nmaps + b];
+        alm[(size_t)b * v.nalm + idx] = make_double2(cm * a.x, m == 0 ? 0.0 : cm * a.y);
+    }
+}
+
+template <int NB>
+int run_adj_group(const shtb_plan_s *p, const double2 *g, int nmaps, int b0, double *u0, double *u1,
+                  double2 *aacc, cudaStream_t st)
+{
+    const BfPlanDev &bf = *p->bf;
+    for (int lev = 1; lev <= bf.depth_max; ++lev) {
+        const int n = bf.level_counts[lev - 1];
+        if (n == 0) continue;
+        const double *uin = ((lev - 1) % 2) ? u1 : u0;
+        double *uout = (lev % 2) ? u1 : u0;
+        const unsigned grid = (unsigned)((n + kBfWarps - 1) / kBfWarps);
+        const size_t smem = sizeof(double) * kBfWarps * shtb::kMaxCand * 2 * NB;
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(bf_adj_level_kernel<NB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bf_adj_level_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, bf.ints,
+                                                                   bf.dbl, uin, g, nmaps, b0, uout);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    if (bf.n_rgroups > 0) {
+        const unsigned grid = (unsigned)((bf.n_rgroups + kBfWarps - 1) / kBfWarps);
+        bf_adj_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(p->view, bf.rgroups, bf.n_rgroups, bf.ritems,
+                                                            bf.ints, bf.dbl, u0, u1, bf.depth_parity, g,
+                                                            nmaps, b0, aacc);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    return SHTB_OK;
+}
+
 }  // namespace
 
 size_t bf_workspace_bytes(const shtb_plan_s *p)
@@ -221,5 +374,27 @@ int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void 
         else { rc = run_group<1>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 1; }
         if (rc) return rc;
     }
+    return SHTB_OK;
+}
+
+int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
+                      int nmaps, cudaStream_t st)
+{
+    const BfPlanDev &bf = *p->bf;
+    const size_t entry = 16;
+    double *u0 = (double *)ws;
+    double *u1 = u0 + (size_t)bf.u_entries * entry;
+    for (int b0 = 0; b0 < nmaps;) {
+        const int left = nmaps - b0;
+        int rc;
+        if (left >= 8) { rc = run_adj_group<8>(p, g, nmaps, b0, u0, u1, aacc, st); b0 += 8; }
+        else if (left >= 4) { rc = run_adj_group<4>(p, g, nmaps, b0, u0, u1, aacc, st); b0 += 4; }
+        else if (left >= 2) { rc = run_adj_group<2>(p, g, nmaps, b0, u0, u1, aacc, st); b0 += 2; }
+        else { rc = run_adj_group<1>(p, g, nmaps, b0, u0, u1, aacc, st); b0 += 1; }
+        if (rc) return rc;
+    }
+    bf_finish_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, aacc, alm, nmaps);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
     return SHTB_OK;
 }

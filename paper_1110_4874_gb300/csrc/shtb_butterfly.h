@@ -33,6 +33,7 @@ struct BfParams {
 // Residual block of one chain (local offsets).
 struct BfRLocal {
     int j0 = 0, nrows = 0, k = 0;
+    int interval = 0;                // index of its row interval at the chain's depth
     bool to_rings = false;           // depth 0: outputs go straight to q^t rings
     long long out_off = 0;           // u entry offset (within the chain's region)
     std::vector<int> rings;
@@ -58,6 +59,7 @@ struct BfChain {
     long long region = 0;            // u entries per buffer
     std::vector<BfRLocal> rblocks;
     std::vector<BfItemLocal> items;  // ordered from the top level down
+    std::vector<std::pair<int, int>> top_rows;   // row intervals at the chosen depth
 };
 
 void compress_chain(const double *Lam, int n, int Z, const BfParams &prm, BfChain *out);
@@ -87,11 +89,20 @@ struct BfItem {
     long long out_off;               // u entry offset of the output, or int offset of q^t entries
 };
 
+// Adjoint: all residual blocks of one (chain, row interval), so that each
+// chain row of a_lm is written by exactly one warp.
+struct BfRGroup {
+    int m, t, r0, r1, nblk;
+    long long blk_off;               // int offset: indices into the residual item list
+};
+
 // Per-plan device data of the compressed operator.
 struct BfPlanDev {
     int depth_max = 0;
     const BfRItem *ritems = nullptr;
     int n_ritems = 0;
+    const BfRGroup *rgroups = nullptr;
+    int n_rgroups = 0;
     std::vector<const BfItem *> level_items;    // level l at [l-1]
     std::vector<int> level_counts;
     const int *ints = nullptr;

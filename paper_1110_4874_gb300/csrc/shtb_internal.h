@@ -136,6 +136,8 @@ int launch_legendre_adjoint(const shtb_plan_s *p, const double2 *qadj, double2 *
                             int nmaps, void *state_ws, cudaStream_t st);
 int launch_alm_finish(const shtb_plan_s *p, const double2 *aacc, double2 *alm, int nmaps,
                       cudaStream_t st);
+int launch_adjoint_parity(const shtb_plan_s *p, const double2 *qadj, double2 *g, int nmaps,
+                          cudaStream_t st);
 size_t legendre_adjoint_state_bytes(const shtb_plan_s *p);
 
 // shtb_phi.cu
@@ -149,6 +151,8 @@ size_t bf_workspace_bytes(const shtb_plan_s *p);
 int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double2 *q,
                     int nmaps, cudaStream_t st);
 void bf_release(shtb_plan_s *p);
+int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
+                      int nmaps, cudaStream_t st);
 
 // shtb_util.cu
 int measure_fp64_peak(int device, double *dfma, double *dmma);

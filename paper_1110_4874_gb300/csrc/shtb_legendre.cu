@@ -403,15 +403,23 @@ size_t legendre_adjoint_state_bytes(const shtb_plan_s *p)
     return sizeof(RecState) * (size_t)(p->lmax + 1) * p->nhalf;
 }
 
+int launch_adjoint_parity(const shtb_plan_s *p, const double2 *qadj, double2 *g, int nmaps,
+                          cudaStream_t st)
+{
+    adjoint_parity_kernel<<<dim3(p->nhalf, nmaps), 256, 0, st>>>(p->view, qadj, g, nmaps);
+    ++p->launches;
+    SHTB_CUDA_TRY(cudaGetLastError());
+    return SHTB_OK;
+}
+
 int launch_legendre_adjoint(const shtb_plan_s *p, const double2 *qadj, double2 *aacc, int nmaps,
                             void *ws, cudaStream_t st)
 {
     // ws: [g: (L+1)*2*Z*nmaps double2][state: (L+1)*Z RecState]
     double2 *g = (double2 *)ws;
     RecState *state = (RecState *)(g + (size_t)(p->lmax + 1) * 2 * p->nhalf * nmaps);
-    adjoint_parity_kernel<<<dim3(p->nhalf, nmaps), 256, 0, st>>>(p->view, qadj, g, nmaps);
-    ++p->launches;
-    SHTB_CUDA_TRY(cudaGetLastError());
+    int rc0 = launch_adjoint_parity(p, qadj, g, nmaps, st);
+    if (rc0) return rc0;
     for (int b0 = 0; b0 < nmaps;) {
         const int left = nmaps - b0;
         int rc;

@@ -258,3 +258,34 @@ def test_autograd_matches_central_differences():
         an = torch.sum(g.real * v.real + g.imag * v.imag).item()
         assert an == pytest.approx(fd, rel=1e-9)
     plan.close()
+
+
+@pytest.mark.parametrize("nside,lmax,eps", COMPRESSED)
+def test_compressed_adjoint_vs_oracle(nside, lmax, eps):
+    """Transposed butterfly: Y^T f within the same tolerance rule."""
+    plan = sh.Plan(nside, lmax, eps)
+    rings = oracle.healpix_rings(nside)
+    f = synthetic.gaussian_map(rings.npix, 2, seed=78)
+    want = oracle.adjoint(rings, lmax, f)
+    got = plan.adjoint(dev(f)).cpu().numpy()
+    tol = 1e-10 if eps <= 1e-12 else 100 * eps
+    for b in range(2):
+        assert rel_rms(want[b], got[b]) <= tol
+    plan.close()
+
+
+@pytest.mark.parametrize("nside,lmax,eps", [(64, 128, 1e-10), (13, 30, 1e-6), (128, 256, 1e-12)])
+def test_compressed_adjoint_is_exact_transpose(nside, lmax, eps):
+    """The compressed adjoint is the transpose of the compressed synthesis:
+    <Y a, f> = <a, Y^T f> to rounding, whatever eps."""
+    plan = sh.Plan(nside, lmax, eps)
+    a = dev(synthetic.gaussian_alm(lmax, 3, seed=21))
+    f = dev(synthetic.gaussian_map(plan.npix, 3, seed=22))
+    lhs = torch.sum(plan.synthesize(a) * f).item()
+    at = plan.adjoint(f)
+    rhs = torch.sum(a.real * at.real + a.imag * at.imag).item()
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    # batches equal single maps
+    for b in range(3):
+        assert torch.equal(at[b], plan.adjoint(f[b:b + 1])[0])
+    plan.close()
