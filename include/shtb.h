@@ -95,6 +95,7 @@ typedef struct {
     double phi_flops_per_map;       /* FP64 flops of the ring FFT stage per map       */
     double build_seconds;           /* host + device time of shtb_plan_create         */
     long long kernel_launches;      /* CUDA kernels this plan has launched so far     */
+    long long n_ident;              /* identity entries of the interpolation matrices  */
     int depth_hist[16];             /* (m, parity) count per butterfly depth          */
 } shtb_plan_stats_t;
 
@@ -167,6 +168,71 @@ int shtb_synthesize_host(shtb_plan plan, const double *alm_host, double *map_hos
 int shtb_adjoint_host(shtb_plan plan, const double *map_host, double *alm_host,
                       int nmaps, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched serving.  A batch holds synthesis requests for any number of
+ * compressed plans (any mix of nside / lmax / eps); requests sharing a plan
+ * are merged along the map axis so that the plan's compressed operator is
+ * read once per group of up to 8 maps (Sec. 3.3: many simultaneous
+ * transforms amortise the precomputed data).  shtb_batch_run executes the
+ * whole batch -- a_lm gather, residual blocks, every butterfly level, parity
+ * combine, ring FFTs -- as ONE persistent kernel launch whose blocks pull
+ * work packs in dependency order from a queue; the launch is captured into a
+ * CUDA graph on the first run and replayed afterwards.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    shtb_plan plan;          /* a compressed plan (eps > 0) on the current device   */
+    const double *alm_dev;   /* [nmaps][nalm] complex128, as shtb_synthesize         */
+    double *map_dev;         /* [nmaps][12 nside^2] float64 (written)                 */
+    int nmaps;
+    int dir;                 /* 0 = synthesis (the only direction served)            */
+} shtb_request;
+
+typedef struct shtb_batch_s *shtb_batch;
+
+typedef struct {
+    int autotune;            /* 1: time the candidate schedules on this batch at
+                                creation (runs it several times) and keep the fastest */
+    int warps_per_block;     /* 4 or 8 (0 = default 4; overridden by autotune)         */
+    int group_width;         /* maps per operator read, 1..8 (default 8)               */
+    int lpt;                 /* 1: largest items first inside each stage               */
+    long long spin_limit;    /* polls before a stage wait gives up (0 = 2e7)           */
+} shtb_batch_opts;
+
+int shtb_batch_opts_init(shtb_batch_opts *opts);
+
+/*
+ * Build a batch over nreq requests (buffers must stay valid while the batch
+ * is used; they are read and written at creation when autotune is on).  The
+ * batch owns its workspace and schedule; creation allocates, runs allocate
+ * nothing.  Errors: SHTB_EINVAL, SHTB_ENOTSUP (uncompressed plan, dir != 0),
+ * SHTB_EMISMATCH, SHTB_ENOMEM, SHTB_ECUDA.
+ */
+int shtb_batch_create(const shtb_request *reqs, int nreq, const shtb_batch_opts *opts,
+                      shtb_batch *out);
+
+/*
+ * Run the batch on `stream` (NULL: the batch's own stream, and wait for it).
+ * The first call captures the launch into a CUDA graph.  Check the outcome
+ * with shtb_batch_status.  Errors: SHTB_EINVAL, SHTB_EMISMATCH, SHTB_ECUDA.
+ */
+int shtb_batch_run(shtb_batch batch, void *stream);
+
+/* Wait for the batch's work on `stream` and report SHTB_ETIMEOUT if a stage
+   wait of the persistent kernel gave up (its bounded spin ran out). */
+int shtb_batch_status(shtb_batch batch, void *stream);
+
+/* Schedule chosen for the batch: warps per block, persistent grid size,
+   number of work packs and the autotuner's best time (ms, 0 if not tuned). */
+int shtb_batch_info(shtb_batch batch, int *warps_per_block, int *grid, int *npacks,
+                    double *tuned_ms);
+
+int shtb_batch_destroy(shtb_batch batch);
+
+/* Private test hook: with on = 1 the batch's first stage claims one item more
+   than it has, so every later stage's bounded wait runs out and the next run
+   ends with SHTB_ETIMEOUT; on = 0 restores it. */
+int shtb_test_batch_stall(shtb_batch batch, int on);
+
 /* Name of an error code (static string). */
 const char *shtb_strerror(int code);
 
@@ -180,6 +246,8 @@ const char *shtb_last_error_message(void);
  *   ms[0] Legendre stage (synthesis), ms[1] ring FFT stage (synthesis),
  *   ms[2] ring FFT stage (adjoint),   ms[3] Legendre stage (adjoint),
  *   ms[4] a_lm staging kernels (scaling / interleave / scatter),
+ *   and, inside ms[0] for compressed plans: ms[5] residual blocks,
+ *   ms[6] butterfly levels, ms[7] parity combine;
  * and the number of profiled calls.  Reading resets the sums.  Up to 4096
  * calls are kept between reads.
  */

@@ -55,12 +55,23 @@ class PlanStats(ctypes.Structure):
                 ("plan_read_bytes", ctypes.c_longlong), ("legendre_flops_per_map", ctypes.c_double),
                 ("recurrence_flops", ctypes.c_double), ("phi_flops_per_map", ctypes.c_double),
                 ("build_seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
-                ("depth_hist", ctypes.c_int * 16)]
+                ("n_ident", ctypes.c_longlong), ("depth_hist", ctypes.c_int * 16)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "depth_hist"}
         d["depth_hist"] = list(self.depth_hist)
         return d
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("alm_dev", ctypes.c_void_p), ("map_dev", ctypes.c_void_p),
+                ("nmaps", ctypes.c_int), ("dir", ctypes.c_int)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int), ("warps_per_block", ctypes.c_int),
+                ("group_width", ctypes.c_int), ("lpt", ctypes.c_int),
+                ("spin_limit", ctypes.c_longlong)]
 
 
 _P = ctypes.c_void_p
@@ -90,6 +101,14 @@ SIGNATURES = {
     "shtb_test_legendre_adjoint": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_host_recurrence": (_I, [_I, _I, _I, _I, _DP]),
     "shtb_synthesize_noalloc": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_batch_opts_init": (_I, [ctypes.POINTER(BatchOpts)]),
+    "shtb_batch_create": (_I, [ctypes.POINTER(Request), _I, ctypes.POINTER(BatchOpts),
+                               ctypes.POINTER(_P)]),
+    "shtb_batch_run": (_I, [_P, _P]),
+    "shtb_batch_status": (_I, [_P, _P]),
+    "shtb_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
+    "shtb_batch_destroy": (_I, [_P]),
+    "shtb_test_batch_stall": (_I, [_P, _I]),
     "shtb_test_host_id": (_I, [_I, _I, _DP, _D, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
     "shtb_test_host_butterfly": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
                                       ctypes.POINTER(ctypes.c_longlong)]),
@@ -238,7 +257,8 @@ def shtb_profile_enable(plan, on: bool) -> None:
     _check(lib().shtb_profile_enable(plan, 1 if on else 0), "shtb_profile_enable")
 
 
-STAGES = ("legendre_synth", "phi_synth", "phi_adjoint", "legendre_adjoint", "staging")
+STAGES = ("legendre_synth", "phi_synth", "phi_adjoint", "legendre_adjoint", "staging",
+          "bf_residual", "bf_levels", "bf_combine")
 
 
 def shtb_profile_read(plan) -> tuple[dict, int]:
@@ -313,6 +333,58 @@ def shtb_test_host_butterfly(nside: int, lmax: int, eps: float, m: int, t: int, 
                                           qe.ctypes.data_as(_DP), info),
            "shtb_test_host_butterfly")
     return q, qe, {"depth": info[0], "n_dense": info[1], "n_r": info[2], "n_ident": info[3]}
+
+
+def shtb_batch_opts_init() -> BatchOpts:
+    o = BatchOpts()
+    _check(lib().shtb_batch_opts_init(ctypes.byref(o)), "shtb_batch_opts_init")
+    return o
+
+
+def shtb_batch_create(requests, autotune: bool = True, warps_per_block: int = 0,
+                      group_width: int = 8, lpt: bool = True, spin_limit: int = 0):
+    """requests: iterable of (plan, alm tensor [nmaps, nalm] complex128, maps tensor
+    [nmaps, npix] float64), all on the current CUDA device."""
+    import torch
+    reqs = list(requests)
+    arr = (Request * len(reqs))()
+    for i, (plan, alm, maps) in enumerate(reqs):
+        h = plan.handle if hasattr(plan, "handle") else plan
+        arr[i].plan = h.value if hasattr(h, "value") else h
+        arr[i].alm_dev = _dptr(alm, torch.complex128, "alm").value
+        arr[i].map_dev = _dptr(maps, torch.float64, "maps").value
+        arr[i].nmaps = int(alm.shape[0])
+        arr[i].dir = 0
+    o = shtb_batch_opts_init()
+    o.autotune, o.warps_per_block, o.group_width = int(autotune), warps_per_block, group_width
+    o.lpt, o.spin_limit = int(lpt), spin_limit
+    h = ctypes.c_void_p()
+    _check(lib().shtb_batch_create(arr, len(reqs), ctypes.byref(o), ctypes.byref(h)),
+           "shtb_batch_create")
+    return h
+
+
+def shtb_batch_run(batch, stream=None) -> None:
+    _check(lib().shtb_batch_run(batch, _stream_handle(stream)), "shtb_batch_run")
+
+
+def shtb_batch_status(batch, stream=None) -> None:
+    _check(lib().shtb_batch_status(batch, _stream_handle(stream)), "shtb_batch_status")
+
+
+def shtb_batch_info(batch) -> dict:
+    w, g, n, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().shtb_batch_info(batch, ctypes.byref(w), ctypes.byref(g), ctypes.byref(n),
+                                 ctypes.byref(t)), "shtb_batch_info")
+    return {"warps_per_block": w.value, "grid": g.value, "npacks": n.value, "tuned_ms": t.value}
+
+
+def shtb_batch_destroy(batch) -> None:
+    _check(lib().shtb_batch_destroy(batch), "shtb_batch_destroy")
+
+
+def shtb_test_batch_stall(batch, on: bool) -> None:
+    _check(lib().shtb_test_batch_stall(batch, int(on)), "shtb_test_batch_stall")
 
 
 # ------------------------------------------------------------ convenience

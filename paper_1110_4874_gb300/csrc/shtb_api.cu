@@ -107,20 +107,12 @@ struct StageTimer {
     shtb_plan_s *p;
     cudaStream_t st;
     int stage;
-    int e0 = -1;
+    int e0;
     StageTimer(shtb_plan_s *pp, cudaStream_t s, int stg) : p(pp), st(s), stage(stg)
     {
-        if (!p->profiling || p->ev_next + 2 > (int)p->ev_pool.size()) return;
-        e0 = p->ev_next;
-        p->ev_next += 2;
-        cudaEventRecord(p->ev_pool[e0], st);
+        e0 = profile_begin(p, st);
     }
-    ~StageTimer()
-    {
-        if (e0 < 0) return;
-        cudaEventRecord(p->ev_pool[e0 + 1], st);
-        p->recs.push_back({stage, e0, e0 + 1});
-    }
+    ~StageTimer() { profile_end(p, st, stage, e0); }
 };
 
 // ------------------------------------------------------------ pipelines
@@ -177,6 +169,22 @@ int run_adjoint(shtb_plan_s *p, const double *map, double2 *alm, int nmaps, cuda
 }
 
 }  // namespace
+
+int profile_begin(shtb_plan_s *p, cudaStream_t st)
+{
+    if (!p->profiling || p->ev_next + 2 > (int)p->ev_pool.size()) return -1;
+    const int e0 = p->ev_next;
+    p->ev_next += 2;
+    cudaEventRecord(p->ev_pool[e0], st);
+    return e0;
+}
+
+void profile_end(shtb_plan_s *p, cudaStream_t st, int stage, int ev)
+{
+    if (ev < 0) return;
+    cudaEventRecord(p->ev_pool[ev + 1], st);
+    p->recs.push_back({stage, ev, ev + 1});
+}
 
 int shtb_fail(int code, const std::string &msg)
 {

@@ -16,16 +16,15 @@
 // per group and used for 2 x maps FMAs.  All stages are FP64-bound on GB300.
 #include <cuda_runtime.h>
 
+#include "shtb_bf_items.cuh"
 #include "shtb_butterfly.h"
 
 namespace {
 
+using shtb_dev::Tile;
+
 constexpr int kBfWarps = 4;
 
-__device__ __forceinline__ long long dalm_off(int L, int m)
-{
-    return (long long)m * (2 * L + 1 - m) / 2 + m;
-}
 
 // ai[idx][b] = a_lm[b][idx] for the group's maps (Im a_l0 = 0, Sec. 2.1)
 __global__ void bf_interleave_kernel(PlanView v, const double2 *__restrict__ alm,
@@ -33,7 +32,7 @@ __global__ void bf_interleave_kernel(PlanView v, const double2 *__restrict__ alm
 {
     const int m = blockIdx.x;
     const int L = v.lmax;
-    const long long off = dalm_off(L, m);
+    const long long off = shtb_dev::alm_off(L, m);
     const int n = L - m + 1;
     for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {
         const int b = i / n, dl = i - b * n;
@@ -50,33 +49,12 @@ bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int
             double *__restrict__ ubuf0, double *__restrict__ ubuf1, const int *__restrict__ depth_par,
             double *__restrict__ qt)
 {
-    constexpr int C = 2 * NB;
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * kBfWarps + (threadIdx.x >> 5);
     if (w >= nitems) return;
     const BfRItem it = items[w];
-    const double *__restrict__ R = dbl + it.data_off;
-    const long long aoff = dalm_off(v.lmax, it.m) + it.t;   // chain row j at aoff + 2j
     double *ubuf = depth_par[it.m * 2 + it.t] ? ubuf1 : ubuf0;
-    for (int s = lane; s < it.k; s += 32) {
-        double acc[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = 0.0;
-        for (int j = 0; j < it.nrows; ++j) {
-            const double r = R[(size_t)j * it.k + s];
-            const double2 *aj = ai + (size_t)(aoff + 2 * (it.j0 + j)) * nmaps + b0;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const double2 a = __ldg(aj + b);
-                acc[2 * b] = fma(r, a.x, acc[2 * b]);
-                acc[2 * b + 1] = fma(r, a.y, acc[2 * b + 1]);
-            }
-        }
-        double *dst = it.to_rings ? qt + (size_t)ints[it.out_off + s] * C
-                                  : ubuf + (size_t)(it.out_off + s) * C;
-#pragma unroll
-        for (int c = 0; c < C; ++c) dst[c] = acc[c];
-    }
+    shtb_dev::bf_r_item<NB, false>(it, v.lmax, ints, dbl, ai, nmaps, b0, ubuf, qt, lane);
 }
 
 template <int NB>
@@ -91,48 +69,8 @@ bf_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__restr
     const int wib = threadIdx.x >> 5;
     const int w = blockIdx.x * kBfWarps + wib;
     if (w >= nitems) return;
-    const BfItem it = items[w];
-    double *out = sout + (size_t)wib * shtb::kMaxCand * C;
-    for (int i = lane; i < it.nc * C; i += 32) out[i] = 0.0;
-    __syncwarp();
-    for (int s = 0; s < 2; ++s) {
-        const int k = it.k[s], nd = it.nd[s];
-        const double *__restrict__ u = uin + (size_t)it.u_off[s] * C;
-        const double *__restrict__ T = dbl + it.T_off[s];
-        const int *__restrict__ dpos = ints + it.dpos_off[s];
-        for (int d = lane; d < nd; d += 32) {
-            double acc[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = 0.0;
-            for (int i = 0; i < k; ++i) {
-                const double t = T[(size_t)i * nd + d];
-                const double *ui = u + (size_t)i * C;
-#pragma unroll
-                for (int c = 0; c < C; ++c) acc[c] = fma(t, __ldg(ui + c), acc[c]);
-            }
-            double *o = out + dpos[d] * C;
-#pragma unroll
-            for (int c = 0; c < C; ++c) o[c] += acc[c];
-        }
-        const int *__restrict__ ipos = ints + it.ipos_off[s];
-        for (int i = lane; i < k; i += 32) {
-            double *o = out + ipos[i] * C;
-            const double *ui = u + (size_t)i * C;
-#pragma unroll
-            for (int c = 0; c < C; ++c) o[c] += __ldg(ui + c);
-        }
-        __syncwarp();
-    }
-    if (it.to_rings) {
-        const int *__restrict__ ent = ints + it.out_off;
-        for (int i = lane; i < it.nc * C; i += 32) {
-            const int cpos = i / C, c = i - cpos * C;
-            qt[(size_t)ent[cpos] * C + c] = out[i];
-        }
-    } else {
-        double *dst = uout + (size_t)it.out_off * C;
-        for (int i = lane; i < it.nc * C; i += 32) dst[i] = out[i];
-    }
+    shtb_dev::bf_level_item<NB, false>(items[w], ints, dbl, uin, uout, qt,
+                                       sout + (size_t)wib * shtb::kMaxCand * C, lane);
 }
 
 // q[b0+b][ring][m]: north ring r gets q^0 + q^1, its mirror q^0 - q^1
@@ -140,23 +78,10 @@ template <int NB>
 __global__ void bf_combine_kernel(PlanView v, const double *__restrict__ qt, double2 *__restrict__ q,
                                   int b0)
 {
-    constexpr int C = 2 * NB;
-    const int m = blockIdx.x;
-    const int L = v.lmax, Z = v.nhalf;
-    const bool odd = m + 1 <= L;    // chain t = 1 exists
-    for (int r = threadIdx.x; r < Z; r += blockDim.x) {
-        const double *e0 = qt + ((size_t)(m * 2 + 0) * Z + r) * C;
-        const double *e1 = qt + ((size_t)(m * 2 + 1) * Z + r) * C;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const double2 x0 = make_double2(e0[2 * b], e0[2 * b + 1]);
-            const double2 x1 = odd ? make_double2(e1[2 * b], e1[2 * b + 1]) : make_double2(0.0, 0.0);
-            double2 *qb = q + (size_t)(b0 + b) * v.nrings * (L + 1);
-            qb[(size_t)r * (L + 1) + m] = make_double2(x0.x + x1.x, x0.y + x1.y);
-            if (r < Z - 1)
-                qb[(size_t)(v.nrings - 1 - r) * (L + 1) + m] = make_double2(x0.x - x1.x, x0.y - x1.y);
-        }
-    }
+    const size_t per_map = (size_t)v.nrings * (v.lmax + 1);
+    shtb_dev::bf_combine_m<NB, false>(blockIdx.x, v.lmax, v.nhalf, v.nrings, qt,
+                                      [&](int b) { return q + (size_t)(b0 + b) * per_map; },
+                                      threadIdx.x, blockDim.x);
 }
 
 template <int NB>
@@ -165,6 +90,7 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
 {
     const BfPlanDev &bf = *p->bf;
     const PlanView &v = p->view;
+    int ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
     if (bf.n_ritems > 0) {
         const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
         bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(v, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
@@ -172,6 +98,8 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
+    profile_end(const_cast<shtb_plan_s *>(p), st, 5, ev);
+    ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
     for (int lev = bf.depth_max; lev >= 1; --lev) {
         const int n = bf.level_counts[lev - 1];
         if (n == 0) continue;
@@ -186,9 +114,12 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
+    profile_end(const_cast<shtb_plan_s *>(p), st, 6, ev);
+    ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
     bf_combine_kernel<NB><<<p->lmax + 1, 256, 0, st>>>(v, qt, q, b0);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
+    profile_end(const_cast<shtb_plan_s *>(p), st, 7, ev);
     return SHTB_OK;
 }
 
@@ -225,26 +156,36 @@ bf_adj_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__r
         for (int i = lane; i < it.nc * C; i += 32) in[i] = src[i];
     }
     __syncwarp();
-    for (int s = 0; s < 2; ++s) {
-        const int k = it.k[s], nd = it.nd[s];
-        const double *__restrict__ T = dbl + it.T_off[s];
-        const int *__restrict__ dpos = ints + it.dpos_off[s];
-        const int *__restrict__ ipos = ints + it.ipos_off[s];
-        for (int i = lane; i < k; i += 32) {
-            double acc[C];
-            const double *xi = in + ipos[i] * C;
+    // rows of both children's u as one list of k0 + k1 rows: identity entry
+    // plus a dot product of the row of T with the candidates' dense part
+    using Tl = Tile<C>;
+    const int il = lane % Tl::LD, cg = lane / Tl::LD;
+    const int k0 = it.k[0], kt = it.k[0] + it.k[1];
+    const int ndmax = max(it.nd[0], it.nd[1]);
+    for (int q0 = 0; q0 < kt; q0 += Tl::LD) {
+        const int q = q0 + il;
+        const bool valid = q < kt;
+        const int s = (valid && q >= k0) ? 1 : 0;
+        const int i = s ? q - k0 : (valid ? q : 0);
+        const int nd = s ? it.nd[1] : it.nd[0];
+        const double *__restrict__ Ti = dbl + (s ? it.T_off[1] : it.T_off[0]) + (size_t)i * nd;
+        const int *__restrict__ dpos = ints + (s ? it.dpos_off[1] : it.dpos_off[0]);
+        const int *__restrict__ ipos = ints + (s ? it.ipos_off[1] : it.ipos_off[0]);
+        double acc[Tl::CPL];
+        const double *xi = in + (valid ? ipos[i] : 0) * C + cg * Tl::CPL;
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = xi[c];
-            const double *Ti = T + (size_t)i * nd;
-            for (int d = 0; d < nd; ++d) {
-                const double t = Ti[d];
-                const double *x = in + dpos[d] * C;
+        for (int c = 0; c < Tl::CPL; ++c) acc[c] = valid ? xi[c] : 0.0;
+        for (int d = 0; d < ndmax; ++d) {
+            const bool live = valid && d < nd;
+            const double t = live ? Ti[d] : 0.0;
+            const double *x = in + (live ? dpos[d] : 0) * C + cg * Tl::CPL;
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[c] = fma(t, x[c], acc[c]);
-            }
-            double *dst = uout + (size_t)(it.u_off[s] + i) * C;
+            for (int c = 0; c < Tl::CPL; ++c) acc[c] = fma(t, x[c], acc[c]);
+        }
+        if (valid) {
+            double *dst = uout + (size_t)((s ? it.u_off[1] : it.u_off[0]) + i) * C + cg * Tl::CPL;
 #pragma unroll
-            for (int c = 0; c < C; ++c) dst[c] = acc[c];
+            for (int c = 0; c < Tl::CPL; ++c) dst[c] = acc[c];
         }
     }
 }
@@ -266,7 +207,7 @@ bf_adj_r_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
     if (w >= ngroups) return;
     const BfRGroup gr = groups[w];
     const double *ubuf = depth_par[gr.m * 2 + gr.t] ? u1 : u0;
-    const long long aoff = dalm_off(v.lmax, gr.m) + gr.t;
+    const long long aoff = shtb_dev::alm_off(v.lmax, gr.m) + gr.t;
     for (int j = gr.r0 + lane; j < gr.r1; j += 32) {
         double acc[C];
 #pragma unroll
@@ -304,7 +245,7 @@ __global__ void bf_finish_kernel(PlanView v, const double2 *__restrict__ aacc,
 {
     const int m = blockIdx.x;
     const int L = v.lmax;
-    const long long off = dalm_off(L, m);
+    const long long off = shtb_dev::alm_off(L, m);
     const int n = L - m + 1;
     const double cm = m == 0 ? 1.0 : 2.0;
     for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {

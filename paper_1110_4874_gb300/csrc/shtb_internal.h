@@ -119,6 +119,11 @@ struct shtb_plan_s {
     int ev_next = 0;
 };
 
+// Stage timing (shtb_profile_enable): event pair around a stage on stream st;
+// profile_begin returns -1 when profiling is off or the event pool is full.
+int profile_begin(shtb_plan_s *p, cudaStream_t st);
+void profile_end(shtb_plan_s *p, cudaStream_t st, int stage, int ev);
+
 // ------------------------------------------------------- host plan build
 // Fills every host-side table and uploads it; defined in shtb_plan_host.cpp.
 int shtb_build_dense_plan(shtb_plan_s *p);

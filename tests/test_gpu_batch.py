@@ -1,0 +1,90 @@
+"""Batched serving: many uneven synthesis requests in one persistent launch
+(captured in a CUDA graph), checked request by request against the
+one-request-per-launch path on the same plans."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1110_4874_gb300 as sh  # noqa: E402
+from paper_1110_4874_gb300 import synthetic  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def setup():
+    rng = np.random.default_rng(3000)
+    plans = {n: sh.Plan(n, 2 * n, 1e-10) for n in (16, 32, 64)}
+    reqs = []
+    for i in range(12):
+        n = int(rng.choice([16, 32, 64]))
+        b = int(rng.integers(1, 9))
+        p = plans[n]
+        alm = torch.from_numpy(synthetic.gaussian_alm(2 * n, b, seed=3000 + 10 * i)).cuda()
+        maps = torch.full((b, p.npix), float("nan"), dtype=torch.float64, device="cuda")
+        reqs.append((p, alm, maps))
+    yield plans, reqs
+    for p in plans.values():
+        p.close()
+
+
+def test_batch_equals_plain_requests(setup):
+    plans, reqs = setup
+    batch = sh.shtb_batch_create(reqs, autotune=True)
+    info = sh.shtb_batch_info(batch)
+    assert info["warps_per_block"] in (4, 8) and info["grid"] > 0 and info["npacks"] > 0
+    torch.cuda.synchronize()
+    for it in range(2):          # first run captures the graph, second replays it
+        for _, _, maps in reqs:
+            maps.fill_(float("nan"))
+        sh.shtb_batch_run(batch)
+        sh.shtb_batch_status(batch)
+        for p, alm, maps in reqs:
+            want = p.synthesize(alm)
+            assert torch.equal(maps, want), f"run {it}"
+    sh.shtb_batch_destroy(batch)
+
+
+def test_batch_on_a_user_stream(setup):
+    plans, reqs = setup
+    batch = sh.shtb_batch_create(reqs[:4], autotune=False, warps_per_block=8)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        sh.shtb_batch_run(batch, s)
+    sh.shtb_batch_status(batch, s)
+    for p, alm, maps in reqs[:4]:
+        assert torch.equal(maps, p.synthesize(alm))
+    sh.shtb_batch_destroy(batch)
+
+
+def test_batch_wait_timeout_reports_status(setup):
+    """A stage wait that never completes (the first stage claims one item
+    more than it has) runs out of its bounded spin: the run ends, the status
+    reports SHTB_ETIMEOUT, and the context stays usable."""
+    plans, reqs = setup
+    batch = sh.shtb_batch_create(reqs[:3], autotune=False, spin_limit=20000)
+    sh.shtb_test_batch_stall(batch, True)
+    sh.shtb_batch_run(batch)
+    with pytest.raises(sh.ShtbError) as e:
+        sh.shtb_batch_status(batch)
+    assert e.value.code == sh.SHTB_ETIMEOUT
+    sh.shtb_test_batch_stall(batch, False)
+    sh.shtb_batch_run(batch)
+    sh.shtb_batch_status(batch)
+    for p, alm, maps in reqs[:3]:
+        assert torch.equal(maps, p.synthesize(alm))
+    sh.shtb_batch_destroy(batch)
+
+
+def test_batch_rejects_bad_requests(setup):
+    plans, reqs = setup
+    dense = sh.Plan(16, 32, 0.0)
+    alm = torch.zeros((1, dense.nalm), dtype=torch.complex128, device="cuda")
+    maps = torch.zeros((1, dense.npix), dtype=torch.float64, device="cuda")
+    with pytest.raises(sh.ShtbError) as e:
+        sh.shtb_batch_create([(dense, alm, maps)])
+    assert e.value.code == sh.SHTB_ENOTSUP
+    with pytest.raises(sh.ShtbError) as e:
+        sh.shtb_batch_create([])
+    assert e.value.code == sh.SHTB_EINVAL
+    dense.close()
