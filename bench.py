@@ -42,15 +42,16 @@ UNIT = "ms/map"
 # divided over 152 SMs at 2070 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
-# DRAM traffic of the dominant kernel from an ncu capture (see profiles/);
-# valid only while the kernel source is unchanged.
+# DRAM traffic of the dominant kernel from an ncu capture (see profiles/),
+# per kernel; valid only while that kernel's source file is unchanged.
 NCU_TRAFFIC = {
-    "kernel": "legendre_synth_kernel<8>",
-    "source": "paper_1110_4874_gb300/csrc/shtb_legendre.cu",
-    "source_sha256": "2716a9eb2679dc0a7730c490c671b800e69d7688a7fb6465ffbe4592e8d7cacb",
-    # 410.5 MB measured at Nside=512, L=1024; every array scales with Nside*L (x16)
-    "bytes_per_launch": 16 * 410_475_008,
-    "profile": "profiles/legendre_synth_nside512_l1024_b8.md",
+    "legendre_synth_kernel": {
+        "source": "paper_1110_4874_gb300/csrc/shtb_legendre.cu",
+        "source_sha256": "2716a9eb2679dc0a7730c490c671b800e69d7688a7fb6465ffbe4592e8d7cacb",
+        # 410.5 MB measured at Nside=512, L=1024; every array scales with Nside*L (x16)
+        "bytes_per_launch": 16 * 410_475_008,
+        "profile": "profiles/legendre_synth_nside512_l1024_b8.md",
+    },
 }
 
 
@@ -249,23 +250,36 @@ def run_ours(args, rank, world, dist):
            "h2d_bytes_per_step": int(alm_h.numel() * alm_h.element_size()),
            "d2h_bytes_per_step": int(maps_h.numel() * maps_h.element_size())}
 
-    # ---- roofline of the dominant kernel (the Legendre stage, FP64-bound)
-    leg_ms = stages["legendre_synth"] / max(ncalls, 1)
+    # ---- roofline of the dominant kernel (FP64-bound on GB300)
     groups = [8] * (B // 8) + ([B % 8] if B % 8 else [])
-    flops = sum(4.0 * st["n_recurrence"] * (1 + g) for g in groups)   # 2 FMA/step + 2 FMA/map
-    achieved = flops / (leg_ms * 1e-3) / 1e12
+    if st["compressed"]:
+        per_step = {   # kernel -> (algorithmic flops per step, ms per step)
+            "bf_level_kernel": (B * (4.0 * st["n_dense"] + 2.0 * st["n_ident"]),
+                                stages["bf_levels"] / max(ncalls, 1)),
+            "bf_r_kernel": (B * 4.0 * st["n_rstored"], stages["bf_residual"] / max(ncalls, 1)),
+        }
+    else:
+        per_step = {"legendre_synth_kernel": (sum(4.0 * st["n_recurrence"] * (1 + g) for g in groups),
+                                              stages["legendre_synth"] / max(ncalls, 1))}
+    kname = max(per_step, key=lambda k: per_step[k][1])
+    flops, kms = per_step[kname]
+    achieved = flops / (kms * 1e-3) / 1e12
     traffic = None
-    if NCU_TRAFFIC["bytes_per_launch"] and NCU_TRAFFIC["source_sha256"] == file_sha256(NCU_TRAFFIC["source"]):
-        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    rec = NCU_TRAFFIC.get(kname)
+    if rec and rec["bytes_per_launch"] and rec["source_sha256"] == file_sha256(rec["source"]):
+        traffic = rec["bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                "kernel": "legendre_synth_kernel (FP64 pipe)",
-                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+                "kernel": f"{kname} (FP64 pipe)",
+                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "per_kernel_tflops": {k: round(f / (t * 1e-3) / 1e12, 4) if t else None
+                                      for k, (f, t) in per_step.items()}}
+    flops_leg = sum(f for f, _ in per_step.values())
     # whole-step HBM view (algorithmic bytes of the batch over the step time)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    step_bytes = (st["plan_read_bytes"] + B * st["nalm"] * 16 * 3 + B * plan.nrings * (L + 1) * 16 * 2
-                  + B * plan.npix * 8)
+    step_bytes = (st["plan_read_bytes"] * len(groups) + B * st["nalm"] * 16 * 3
+                  + B * plan.nrings * (L + 1) * 16 * 2 + B * plan.npix * 8)
     step_ms = ms_total / args.steps
     hbm = {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (step_ms * 1e-3) / 1e9, 1),
            "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)" if hbm_peak else None,
@@ -289,7 +303,9 @@ def run_ours(args, rank, world, dist):
                     "plan_build_s": round(plan_s, 2),
                     "plan_device_gb": round(st["plan_device_bytes"] / 1e9, 3),
                     "n_recurrence": st["n_recurrence"], "n_dense": st["n_dense"],
-                    "legendre_flops_per_launch": flops},
+                    "n_rstored": st["n_rstored"], "n_ident": st["n_ident"],
+                    "depth_hist": st["depth_hist"][:12],
+                    "legendre_flops_per_step": flops_leg},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, cores, sample = oracle_sample(N, L, 1, args.cpu_rings, seed=2000)

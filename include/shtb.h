@@ -247,8 +247,8 @@ const char *shtb_last_error_message(void);
  *   ms[2] ring FFT stage (adjoint),   ms[3] Legendre stage (adjoint),
  *   ms[4] a_lm staging kernels (scaling / interleave / scatter),
  *   and, inside ms[0] for compressed plans: ms[5] residual blocks,
- *   ms[6] butterfly levels, ms[7] parity combine;
- * and the number of profiled calls.  Reading resets the sums.  Up to 4096
+ *   ms[6] butterfly levels (ms[7] is unused);
+ * and the number of profiled transforms.  Reading resets the sums.  Up to 4096
  * calls are kept between reads.
  */
 int shtb_profile_enable(shtb_plan plan, int on);

@@ -121,10 +121,11 @@ int run_synthesis(shtb_plan_s *p, const double2 *alm, double *map, int nmaps, cu
     int rc = ensure_ws(p, nmaps);
     if (rc) return rc;
     Workspace w = carve(p, nmaps);
+    if (p->profiling) ++p->prof_calls;
     if (p->bf) {
-        // compressed operator (Sec. 3.2): residual blocks, butterfly levels, parity combine
-        StageTimer t(p, st, 0);
-        if ((rc = launch_bf_synth(p, alm, w.ap, w.bf, w.q, nmaps, st))) return rc;
+        // compressed operator (Sec. 3.2): per map group residual blocks, butterfly
+        // levels, then the ring stage reading both parity halves directly
+        return launch_bf_synth(p, alm, w.ap, w.bf, map, nmaps, st);
     } else {
         {
             StageTimer t(p, st, 4);
@@ -144,6 +145,7 @@ int run_adjoint(shtb_plan_s *p, const double *map, double2 *alm, int nmaps, cuda
 {
     int rc = ensure_ws(p, nmaps);
     if (rc) return rc;
+    if (p->profiling) ++p->prof_calls;
     Workspace w = carve(p, nmaps);
     {
         StageTimer t(p, st, 2);
@@ -371,8 +373,9 @@ int shtb_profile_read(shtb_plan p, double *ms, int nstages, int *ncalls)
         float t = 0.f;
         SHTB_CUDA_TRY(cudaEventElapsedTime(&t, p->ev_pool[r.ev0], p->ev_pool[r.ev1]));
         if (r.stage < nstages) ms[r.stage] += t;
-        if (r.stage == 0 || r.stage == 2) ++calls;
     }
+    calls = p->prof_calls;
+    p->prof_calls = 0;
     p->recs.clear();
     p->ev_next = 0;
     if (ncalls) *ncalls = calls;

@@ -21,10 +21,9 @@
 #include <string>
 #include <vector>
 
-#include "shtb_bf_items.cuh"
+#include "shtb_batch_items.cuh"
 #include "shtb_butterfly.h"
 #include "shtb_internal.h"
-#include "shtb_phi_items.cuh"
 
 namespace {
 
@@ -84,19 +83,19 @@ __device__ void warp_item(const BatchDev &bd, const BatchWork &w, double *wsm, i
     case W_RES: {
         const BfRItem it = G.ritems[w.idx];
         double *ubuf = G.depth_parity[it.m * 2 + it.t] ? M.u1 : M.u0;
-        shtb_dev::bf_r_item<NB, true>(it, G.v.lmax, G.ints, G.dbl, G.ai, G.nmaps, M.b0, ubuf, M.qt, lane);
+        shtb_bdev::bf_r_item<NB, true>(it, G.v.lmax, G.ints, G.dbl, G.ai, G.nmaps, M.b0, ubuf, M.qt, lane);
         break;
     }
     case W_LEVEL: {
         const double *uin = (w.level % 2) ? M.u1 : M.u0;
         double *uout = ((w.level - 1) % 2) ? M.u1 : M.u0;
-        shtb_dev::bf_level_item<NB, true>(G.litems[w.level - 1][w.idx], G.ints, G.dbl, uin, uout, M.qt,
+        shtb_bdev::bf_level_item<NB, true>(G.litems[w.level - 1][w.idx], G.ints, G.dbl, uin, uout, M.qt,
                                           wsm, lane);
         break;
     }
     case W_COMBINE: {
         const size_t per_map = (size_t)G.v.nrings * (G.v.lmax + 1);
-        shtb_dev::bf_combine_m<NB, true>(w.idx, G.v.lmax, G.v.nhalf, G.v.nrings, M.qt,
+        shtb_bdev::bf_combine_m<NB, true>(w.idx, G.v.lmax, G.v.nhalf, G.v.nrings, M.qt,
                                          [&](int b) { return G.q + (size_t)(M.b0 + b) * per_map; }, lane,
                                          32);
         break;
@@ -111,7 +110,7 @@ __device__ void gather_item(const BatchDev &bd, const BatchWork &w, int lane)
 {
     const BatchGroupDev &G = bd.groups[w.g];
     const int m = w.idx, L = G.v.lmax;
-    const long long off = shtb_dev::alm_off(L, m);
+    const long long off = shtb_bdev::alm_off(L, m);
     const int n = L - m + 1;
     for (int i = lane; i < n * G.nmaps; i += 32) {
         const int b = i / n, dl = i - b * n;
@@ -156,9 +155,9 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchDev bd)
             const double2 *qr = G.q + ((size_t)b * G.v.nrings + ring) * (G.v.lmax + 1);
             double *out = G.map_of_map[b] + G.v.ring_start[ring];
             if (G.v.ring_M[ring] > 0)
-                shtb_dev::phi_synth_ring<true, true>(G.v, ring, qr, out, reinterpret_cast<double2 *>(bsm));
+                shtb_bdev::phi_synth_ring<true, true>(G.v, ring, qr, out, reinterpret_cast<double2 *>(bsm));
             else
-                shtb_dev::phi_synth_ring<false, true>(G.v, ring, qr, out, reinterpret_cast<double2 *>(bsm));
+                shtb_bdev::phi_synth_ring<false, true>(G.v, ring, qr, out, reinterpret_cast<double2 *>(bsm));
         } else if (wib < P.count) {
             const BatchWork w = bd.work[P.first + wib];
             if (w.type == W_GATHER) {

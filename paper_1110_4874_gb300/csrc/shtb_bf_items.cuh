@@ -1,8 +1,8 @@
-// Per-work-item device bodies of the butterfly synthesis (Sec. 3.2), shared
-// by the stand-alone stage kernels (shtb_butterfly.cu) and the persistent
-// batch kernel (shtb_batch.cu).  CG = true reads data produced earlier in the
-// same launch through L2 only (ld.global.cg), as the persistent kernel must:
-// L1 is not coherent between SMs within one launch.
+// Per-work-item device bodies of the butterfly synthesis (Sec. 3.2) used by
+// the stage kernels of shtb_butterfly.cu (the persistent batch kernel keeps
+// its own copies, shtb_batch_items.cuh).  CG = true reads data through L2
+// only (ld.global.cg), for data produced earlier in the same launch: L1 is
+// not coherent between SMs within one launch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,10 +35,22 @@ __device__ __forceinline__ long long alm_off(int L, int m)
     return (long long)m * (2 * L + 1 - m) / 2 + m;
 }
 
+// q^t of a map group is stored map-major as complex values:
+// qt[((b * 2 + t) * nhalf + r) * (L + 1) + m], so the ring stage reads each
+// map's q_m of one ring contiguously in m.  Leaf outputs are addressed by the
+// entry e = (m * 2 + t) * nhalf + r; this writes the C = 2 NB components of e.
+__device__ __forceinline__ void qt_store(double *qt, long long e, int nhalf, int L, int c, double v)
+{
+    const long long mt = e / nhalf, r = e - mt * nhalf;
+    const long long m = mt >> 1, t = mt & 1;
+    const int b = c >> 1;
+    qt[((((long long)b * 2 + t) * nhalf + r) * (L + 1) + m) * 2 + (c & 1)] = v;
+}
+
 // u = R^T a over one residual block (lane tile over the block's k columns).
 // ai: [idx][nmaps] complex, the group's maps at b0 .. b0+NB-1.
 template <int NB, bool CG>
-__device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, const int *__restrict__ ints,
+__device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, int nhalf, const int *__restrict__ ints,
                                           const double *__restrict__ dbl, const double2 *ai, int nmaps,
                                           int b0, double *ubuf, double *qt, int lane)
 {
@@ -53,6 +65,7 @@ __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, const int *_
         for (int r = 0; r < Tl::RPL; ++r)
 #pragma unroll
             for (int c = 0; c < Tl::CPL; ++c) acc[r][c] = 0.0;
+#pragma unroll 2
         for (int j = 0; j < it.nrows; ++j) {
             const double *aj = reinterpret_cast<const double *>(
                 ai + (size_t)(aoff + 2 * (it.j0 + j)) * nmaps + b0) + cg * Tl::CPL;
@@ -71,25 +84,38 @@ __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, const int *_
         for (int r = 0; r < Tl::RPL; ++r) {
             const int sidx = s0 + sl + r * Tl::LD;
             if (sidx >= it.k) continue;
-            double *dst = it.to_rings ? qt + (size_t)ints[it.out_off + sidx] * C
-                                      : ubuf + (size_t)(it.out_off + sidx) * C;
+            if (it.to_rings) {
+                const long long e = ints[it.out_off + sidx];
 #pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) dst[cg * Tl::CPL + c] = acc[r][c];
+                for (int c = 0; c < Tl::CPL; ++c) qt_store(qt, e, nhalf, L, cg * Tl::CPL + c, acc[r][c]);
+            } else {
+                double *dst = ubuf + (size_t)(it.out_off + sidx) * C;
+#pragma unroll
+                for (int c = 0; c < Tl::CPL; ++c) dst[cg * Tl::CPL + c] = acc[r][c];
+            }
         }
     }
 }
 
 // One level item: v = T_top^T u_top + T_bot^T u_bot over the shared
 // candidate list, written to the parent level's u (or to q^t at level 1).
-// out: this warp's shared-memory scratch of kMaxCand x C doubles.
+// out: this warp's shared-memory scratch of nc x (C + 1) doubles (the odd row
+// stride spreads the lanes' rows over the banks).
+template <int C>
+__host__ __device__ constexpr int out_stride()
+{
+    return C + 1;
+}
+
 template <int NB, bool CG>
-__device__ __forceinline__ void bf_level_item(const BfItem &it, const int *__restrict__ ints,
+__device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
                                               const double *__restrict__ dbl, const double *uin,
                                               double *uout, double *qt, double *out, int lane)
 {
     constexpr int C = 2 * NB;
+    constexpr int OS = out_stride<C>();
     using Tl = Tile<C>;
-    for (int i = lane; i < it.nc * C; i += 32) out[i] = 0.0;
+    for (int i = lane; i < it.nc * OS; i += 32) out[i] = 0.0;
     __syncwarp();
     // dense parts of both children as one list of nd0 + nd1 rows (LD rows per
     // pass), each row a k-long dot product with its child's u; the top child's
@@ -109,6 +135,7 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, const int *__res
         double acc[Tl::CPL];
 #pragma unroll
         for (int c = 0; c < Tl::CPL; ++c) acc[c] = 0.0;
+#pragma unroll 4
         for (int i = 0; i < kmax; ++i) {
             const bool live = valid && i < k;
             const double t = live ? T[(size_t)i * nd] : 0.0;
@@ -116,7 +143,7 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, const int *__res
 #pragma unroll
             for (int c = 0; c < Tl::CPL; ++c) acc[c] = fma(t, ldp<CG>(ui + c), acc[c]);
         }
-        double *o = out + (valid ? ints[(s ? it.dpos_off[1] : it.dpos_off[0]) + d] : 0) * C + cg * Tl::CPL;
+        double *o = out + (valid ? ints[(s ? it.dpos_off[1] : it.dpos_off[0]) + d] : 0) * OS + cg * Tl::CPL;
         if (valid && s == 0) {
 #pragma unroll
             for (int c = 0; c < Tl::CPL; ++c) o[c] += acc[c];
@@ -134,7 +161,7 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, const int *__res
         const double *u = uin + (size_t)(s ? it.u_off[1] : it.u_off[0]) * C;
         const int *__restrict__ ipos = ints + (s ? it.ipos_off[1] : it.ipos_off[0]);
         for (int i = lane; i < k; i += 32) {
-            double *o = out + ipos[i] * C;
+            double *o = out + ipos[i] * OS;
             const double *ui = u + (size_t)i * C;
 #pragma unroll
             for (int c = 0; c < C; ++c) o[c] += ldp<CG>(ui + c);
@@ -144,37 +171,17 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, const int *__res
     if (it.to_rings) {
         const int *__restrict__ ent = ints + it.out_off;
         for (int i = lane; i < it.nc * C; i += 32) {
-            const int cpos = i / C, c = i - cpos * C;
-            qt[(size_t)ent[cpos] * C + c] = out[i];
+            const int c = i / it.nc, cpos = i - c * it.nc;
+            qt_store(qt, ent[cpos], nhalf, L, c, out[cpos * OS + c]);
         }
     } else {
         double *dst = uout + (size_t)it.out_off * C;
-        for (int i = lane; i < it.nc * C; i += 32) dst[i] = out[i];
-    }
-    __syncwarp();
-}
-
-// q[b][ring][m] of order m for half-rings r = r0, r0 + rs, ...: north ring r
-// gets q^0 + q^1, its mirror q^0 - q^1 (Eq. q-even-odd2); q_of(b) gives map
-// b's q base ([nrings][L+1] complex).
-template <int NB, bool CG, class QOf>
-__device__ __forceinline__ void bf_combine_m(int m, int L, int Z, int nrings, const double *qt,
-                                             QOf q_of, int r0, int rs)
-{
-    constexpr int C = 2 * NB;
-    const bool odd = m + 1 <= L;    // chain t = 1 exists
-    for (int r = r0; r < Z; r += rs) {
-        const double *e0 = qt + ((size_t)(m * 2 + 0) * Z + r) * C;
-        const double *e1 = qt + ((size_t)(m * 2 + 1) * Z + r) * C;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const double x0 = ldp<CG>(e0 + 2 * b), y0 = ldp<CG>(e0 + 2 * b + 1);
-            const double x1 = odd ? ldp<CG>(e1 + 2 * b) : 0.0, y1 = odd ? ldp<CG>(e1 + 2 * b + 1) : 0.0;
-            double2 *qb = q_of(b);
-            qb[(size_t)r * (L + 1) + m] = make_double2(x0 + x1, y0 + y1);
-            if (r < Z - 1) qb[(size_t)(nrings - 1 - r) * (L + 1) + m] = make_double2(x0 - x1, y0 - y1);
+        for (int i = lane; i < it.nc * C; i += 32) {
+            const int cpos = i / C, c = i - cpos * C;
+            dst[i] = out[cpos * OS + c];
         }
     }
+    __syncwarp();
 }
 
 }  // namespace shtb_dev

@@ -9,8 +9,8 @@
 //                    level's two u vectors (or q^t on a leaf block at level 1);
 //                    identity part = adds, dense part = k x nd dot products
 //                    (Appendix: the identity-embedded interpolation matrices);
-//   bf_combine_kernel q_m(+z) = q^0 + q^1, q_m(-z) = q^0 - q^1 (Eq. q-even-odd2)
-//                    into the ring-major q of the ring stage.
+// and the ring stage of each map group then reads q_m(+z) = q^0 + q^1 and
+// q_m(-z) = q^0 - q^1 (Eq. q-even-odd2) straight from the two parity halves.
 // One warp per work item; all maps of a group (up to 8, 2 real components
 // each) are carried per entry so every stored matrix element is read once
 // per group and used for 2 x maps FMAs.  All stages are FP64-bound on GB300.
@@ -54,43 +54,34 @@ bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int
     if (w >= nitems) return;
     const BfRItem it = items[w];
     double *ubuf = depth_par[it.m * 2 + it.t] ? ubuf1 : ubuf0;
-    shtb_dev::bf_r_item<NB, false>(it, v.lmax, ints, dbl, ai, nmaps, b0, ubuf, qt, lane);
+    shtb_dev::bf_r_item<NB, false>(it, v.lmax, v.nhalf, ints, dbl, ai, nmaps, b0, ubuf, qt, lane);
 }
 
 template <int NB>
 __global__ void __launch_bounds__(32 * kBfWarps)
-bf_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__restrict__ ints,
-                const double *__restrict__ dbl, const double *__restrict__ uin,
-                double *__restrict__ uout, double *__restrict__ qt)
+bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, int maxnc,
+                const int *__restrict__ ints, const double *__restrict__ dbl,
+                const double *__restrict__ uin, double *__restrict__ uout, double *__restrict__ qt)
 {
-    constexpr int C = 2 * NB;
-    extern __shared__ double sout[];     // [kBfWarps][kMaxCand * C]
+    constexpr int OS = shtb_dev::out_stride<2 * NB>();
+    extern __shared__ double sout[];     // [kBfWarps][maxnc * OS]
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int w = blockIdx.x * kBfWarps + wib;
     if (w >= nitems) return;
-    shtb_dev::bf_level_item<NB, false>(items[w], ints, dbl, uin, uout, qt,
-                                       sout + (size_t)wib * shtb::kMaxCand * C, lane);
-}
-
-// q[b0+b][ring][m]: north ring r gets q^0 + q^1, its mirror q^0 - q^1
-template <int NB>
-__global__ void bf_combine_kernel(PlanView v, const double *__restrict__ qt, double2 *__restrict__ q,
-                                  int b0)
-{
-    const size_t per_map = (size_t)v.nrings * (v.lmax + 1);
-    shtb_dev::bf_combine_m<NB, false>(blockIdx.x, v.lmax, v.nhalf, v.nrings, qt,
-                                      [&](int b) { return q + (size_t)(b0 + b) * per_map; },
-                                      threadIdx.x, blockDim.x);
+    shtb_dev::bf_level_item<NB, false>(items[w], L, nhalf, ints, dbl, uin, uout, qt,
+                                       sout + (size_t)wib * maxnc * OS, lane);
 }
 
 template <int NB>
 int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
-              double *qt, double2 *q, cudaStream_t st)
+              double *qt, double *map, cudaStream_t st)
 {
     const BfPlanDev &bf = *p->bf;
     const PlanView &v = p->view;
-    int ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
+    shtb_plan_s *pp = const_cast<shtb_plan_s *>(p);
+    const int ev_leg = profile_begin(pp, st);
+    int ev = profile_begin(pp, st);
     if (bf.n_ritems > 0) {
         const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
         bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(v, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
@@ -98,29 +89,31 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
-    profile_end(const_cast<shtb_plan_s *>(p), st, 5, ev);
-    ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
+    profile_end(pp, st, 5, ev);
+    ev = profile_begin(pp, st);
     for (int lev = bf.depth_max; lev >= 1; --lev) {
         const int n = bf.level_counts[lev - 1];
         if (n == 0) continue;
         double *uin = (lev % 2) ? u1 : u0;
         double *uout = ((lev - 1) % 2) ? u1 : u0;
         const unsigned grid = (unsigned)((n + kBfWarps - 1) / kBfWarps);
-        const size_t smem = sizeof(double) * kBfWarps * shtb::kMaxCand * 2 * NB;
+        const int maxnc = bf.level_maxnc[lev - 1];
+        const size_t smem = sizeof(double) * kBfWarps * maxnc * shtb_dev::out_stride<2 * NB>();
         SHTB_CUDA_TRY(cudaFuncSetAttribute(bf_level_kernel<NB>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        bf_level_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, bf.ints,
-                                                               bf.dbl, uin, uout, qt);
+        bf_level_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, p->lmax,
+                                                               p->nhalf, maxnc, bf.ints, bf.dbl, uin,
+                                                               uout, qt);
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
-    profile_end(const_cast<shtb_plan_s *>(p), st, 6, ev);
-    ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
-    bf_combine_kernel<NB><<<p->lmax + 1, 256, 0, st>>>(v, qt, q, b0);
-    SHTB_CUDA_TRY(cudaGetLastError());
-    ++p->launches;
-    profile_end(const_cast<shtb_plan_s *>(p), st, 7, ev);
-    return SHTB_OK;
+    profile_end(pp, st, 6, ev);
+    profile_end(pp, st, 0, ev_leg);
+    // ring stage of this group straight from q^0, q^1 (parity combine fused)
+    ev = profile_begin(pp, st);
+    int rc = launch_phi_synth_qt(p, qt, NB, map, b0, st);
+    profile_end(pp, st, 1, ev);
+    return rc;
 }
 
 
@@ -295,7 +288,7 @@ size_t bf_workspace_bytes(const shtb_plan_s *p)
     return (2 * (size_t)p->bf->u_entries + (size_t)p->bf->qt_entries) * entry + 512;
 }
 
-int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double2 *q,
+int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
                     int nmaps, cudaStream_t st)
 {
     const BfPlanDev &bf = *p->bf;
@@ -303,16 +296,18 @@ int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void 
     double *u0 = (double *)ws;
     double *u1 = u0 + (size_t)bf.u_entries * entry;
     double *qt = u1 + (size_t)bf.u_entries * entry;
+    const int ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
     bf_interleave_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ai, nmaps);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
+    profile_end(const_cast<shtb_plan_s *>(p), st, 4, ev);
     for (int b0 = 0; b0 < nmaps;) {
         const int left = nmaps - b0;
         int rc;
-        if (left >= 8) { rc = run_group<8>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 8; }
-        else if (left >= 4) { rc = run_group<4>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 4; }
-        else if (left >= 2) { rc = run_group<2>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 2; }
-        else { rc = run_group<1>(p, ai, nmaps, b0, u0, u1, qt, q, st); b0 += 1; }
+        if (left >= 8) { rc = run_group<8>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 8; }
+        else if (left >= 4) { rc = run_group<4>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 4; }
+        else if (left >= 2) { rc = run_group<2>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 2; }
+        else { rc = run_group<1>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 1; }
         if (rc) return rc;
     }
     return SHTB_OK;

@@ -105,6 +105,7 @@ struct BfPlanDev {
     int n_rgroups = 0;
     std::vector<const BfItem *> level_items;    // level l at [l-1]
     std::vector<int> level_counts;
+    std::vector<int> level_maxnc;               // largest candidate list per level
     const int *ints = nullptr;
     const double *dbl = nullptr;
     const int *depth_parity = nullptr;   // per chain (m*2 + t): depth % 2 (u buffer of its R output)

@@ -117,6 +117,7 @@ struct shtb_plan_s {
     struct Rec { int stage; int ev0, ev1; };
     std::vector<Rec> recs;
     int ev_next = 0;
+    int prof_calls = 0;      // transforms run since the last profile read
 };
 
 // Stage timing (shtb_profile_enable): event pair around a stage on stream st;
@@ -150,10 +151,12 @@ int launch_phi_synth(const shtb_plan_s *p, const double2 *q, double *map, int nm
                      cudaStream_t st);
 int launch_phi_adjoint(const shtb_plan_s *p, const double *map, double2 *q, int nmaps,
                        cudaStream_t st);
+int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0,
+                        cudaStream_t st);
 
 // shtb_butterfly.cu
 size_t bf_workspace_bytes(const shtb_plan_s *p);
-int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double2 *q,
+int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
                     int nmaps, cudaStream_t st);
 void bf_release(shtb_plan_s *p);
 int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,

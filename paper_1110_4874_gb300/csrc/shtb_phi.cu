@@ -38,6 +38,20 @@ phi_synth_kernel(PlanView v, const int *__restrict__ rings, const double2 *__res
                                           map + (size_t)b * v.npix + v.ring_start[ring], sm);
 }
 
+// ring stage of a compressed plan's map group, straight from the parity
+// halves q^0, q^1 of the butterfly output (no separate combine pass)
+template <bool BLUE>
+__global__ void __launch_bounds__(kPhiThreads)
+phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ qt,
+                    double *__restrict__ map, int b0)
+{
+    extern __shared__ double2 sm[];
+    const int ring = rings[blockIdx.x];
+    const int b = blockIdx.y;
+    shtb_dev::phi_synth_ring_qt<BLUE, false>(v, ring, qt, b,
+                                             map + (size_t)(b0 + b) * v.npix + v.ring_start[ring], sm);
+}
+
 template <bool BLUE>
 __global__ void __launch_bounds__(kPhiThreads)
 phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__restrict__ map,
@@ -126,6 +140,31 @@ int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int 
 }
 
 }  // namespace
+
+int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0,
+                        cudaStream_t st)
+{
+    const double2 *q2 = (const double2 *)qt;
+    if (!p->pow2_rings.empty()) {
+        const size_t smem = sizeof(double2) * (size_t)p->max_K_pow2;
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        phi_synth_qt_kernel<false><<<dim3((unsigned)p->pow2_rings.size(), (unsigned)nb), kPhiThreads,
+                                     smem, st>>>(p->view, p->d_pow2_rings, q2, map, b0);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    if (!p->blue_rings.empty()) {
+        const size_t smem = sizeof(double2) * (size_t)p->max_M_blue;
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        phi_synth_qt_kernel<true><<<dim3((unsigned)p->blue_rings.size(), (unsigned)nb), kPhiThreads,
+                                    smem, st>>>(p->view, p->d_blue_rings, q2, map, b0);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    return SHTB_OK;
+}
 
 int launch_phi_synth(const shtb_plan_s *p, const double2 *q, double *map, int nmaps, cudaStream_t st)
 {

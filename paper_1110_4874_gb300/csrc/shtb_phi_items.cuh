@@ -1,7 +1,7 @@
 // Device bodies of the ring stage (Eq. sh-baseline, Eq. tau): complex
-// helpers, the radix-2 and Bluestein FFTs in shared memory and the per-ring
-// synthesis, shared by the stand-alone ring kernels (shtb_phi.cu) and the
-// persistent batch kernel (shtb_batch.cu).
+// helpers, the radix-4 and Bluestein FFTs in shared memory and the per-ring
+// synthesis used by the ring kernels of shtb_phi.cu (the persistent batch
+// kernel keeps its own copies, shtb_batch_items.cuh).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,59 +36,103 @@ __device__ __forceinline__ double2 ring_root(const double2 *__restrict__ T, int 
 template <bool CG>
 __device__ __forceinline__ double2 ldq(const double2 *p)
 {
-    return CG ? __ldcg(p) : *p;
+    return CG ? __ldcg(p) : __ldg(p);
 }
 
-template <bool CG>
-__device__ double2 fold_G(const double2 *__restrict__ qr, int L, int J, int s, int r)
+template <class QAt>
+__device__ double2 fold_G(QAt qat, int L, int J, int s, int r)
 {
     double2 acc = make_double2(0.0, 0.0);
     int t = 0;
     for (int m = r; m <= L; m += J, ++t) {
-        double2 v = ldq<CG>(qr + m);
+        double2 v = qat(m);
         if (s & t & 1) { v.x = -v.x; v.y = -v.y; }
         acc = cadd(acc, v);
     }
     for (int tt = 1;; ++tt) {           // m = r - tt J < 0: q_m = conj(q_{-m})
         const int mp = tt * J - r;
         if (mp > L) break;
-        double2 v = cconj(ldq<CG>(qr + mp));
+        double2 v = cconj(qat(mp));
         if (s & tt & 1) { v.x = -v.x; v.y = -v.y; }
         acc = cadd(acc, v);
     }
     return acc;
 }
 
-// radix-2 decimation in time, positive exponent: bit-reversed in, natural out
+__device__ __forceinline__ double2 times_mi(double2 a) { return make_double2(a.y, -a.x); }
+
+__device__ __forceinline__ int ilog2(int m)
+{
+    return 31 - __clz(m);
+}
+
+// Decimation in time, positive exponent: bit-reversed in, natural out.
+// Radix-4 passes, each fusing the radix-2 stages of half-size h and 2h: with
+// t1 = W^{2j} b, t2 = W^{j} c, t3 = W^{3j} d (W the 4h-th root),
+//   a' = (a+t1) + (t2+t3),  b' = (a-t1) + i (t2-t3),
+//   c' = (a+t1) - (t2+t3),  d' = (a-t1) - i (t2-t3);
+// an odd number of stages starts with one twiddle-free radix-2 pass.
 static __device__ void fft_dit_inverse(double2 *x, int M, const double2 *__restrict__ W, int Wlen)
 {
-    for (int half = 1; half < M; half <<= 1) {
+    int h = 1;
+    if (ilog2(M) & 1) {
         __syncthreads();
-        const int stride = Wlen / (2 * half);
         for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
-            const int j = b & (half - 1);
-            const int i0 = ((b - j) << 1) + j, i1 = i0 + half;
-            const double2 t = cmul(__ldg(W + (size_t)j * stride), x[i1]);
-            const double2 u = x[i0];
-            x[i0] = cadd(u, t);
-            x[i1] = csub(u, t);
+            const double2 u = x[2 * b], v = x[2 * b + 1];
+            x[2 * b] = cadd(u, v);
+            x[2 * b + 1] = csub(u, v);
+        }
+        h = 2;
+    }
+    for (; h < M; h *= 4) {
+        __syncthreads();
+        const int S = Wlen / (4 * h);
+        for (int b = threadIdx.x; b < M / 4; b += blockDim.x) {
+            const int j = b % h;
+            const int base = (b - j) * 4 + j;
+            const double2 a = x[base];
+            const double2 t1 = cmul(__ldg(W + (size_t)2 * j * S), x[base + h]);
+            const double2 t2 = cmul(__ldg(W + (size_t)j * S), x[base + 2 * h]);
+            const double2 t3 = cmul(__ldg(W + (size_t)3 * j * S), x[base + 3 * h]);
+            const double2 p = cadd(a, t1), m = csub(a, t1);
+            const double2 sp = cadd(t2, t3), sm = times_i(csub(t2, t3));
+            x[base] = cadd(p, sp);
+            x[base + h] = cadd(m, sm);
+            x[base + 2 * h] = csub(p, sp);
+            x[base + 3 * h] = csub(m, sm);
         }
     }
     __syncthreads();
 }
 
-// radix-2 decimation in frequency, negative exponent: natural in, bit-reversed out
+// Decimation in frequency, negative exponent: natural in, bit-reversed out.
+// Radix-4 passes fusing the stages of half-size H and H/2 (w = conj of the
+// 2H-th root): with s0 = a+c, s1 = a-c, s2 = b+d, s3 = b-d,
+//   a' = s0+s2,  b' = (s0-s2) w^{2j},  c' = (s1 - i s3) w^{j},  d' = (s1 + i s3) w^{3j};
+// an odd number of stages ends with one twiddle-free radix-2 pass.
 static __device__ void fft_dif_forward(double2 *x, int M, const double2 *__restrict__ W, int Wlen)
 {
-    for (int half = M / 2; half >= 1; half >>= 1) {
+    int H = M / 2;
+    for (; H >= 2; H /= 4) {
         __syncthreads();
-        const int stride = Wlen / (2 * half);
+        const int S = Wlen / (2 * H), Q = H / 2;
+        for (int b = threadIdx.x; b < M / 4; b += blockDim.x) {
+            const int j = b % Q;
+            const int base = (b - j) * 4 + j;
+            const double2 a = x[base], bb = x[base + Q], c = x[base + H], d = x[base + H + Q];
+            const double2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(bb, d), s3 = csub(bb, d);
+            x[base] = cadd(s0, s2);
+            x[base + Q] = cmul_conj(csub(s0, s2), __ldg(W + (size_t)2 * j * S));
+            x[base + H] = cmul_conj(cadd(s1, times_mi(s3)), __ldg(W + (size_t)j * S));
+            x[base + H + Q] = cmul_conj(cadd(s1, times_i(s3)), __ldg(W + (size_t)3 * j * S));
+        }
+    }
+    if (H == 1) {
+        __syncthreads();
         for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
-            const int j = b & (half - 1);
-            const int i0 = ((b - j) << 1) + j, i1 = i0 + half;
-            const double2 u = x[i0], w = x[i1];
-            x[i0] = cadd(u, w);
-            x[i1] = cmul_conj(csub(u, w), __ldg(W + (size_t)j * stride));
+            const double2 u = x[2 * b], v = x[2 * b + 1];
+            x[2 * b] = cadd(u, v);
+            x[2 * b + 1] = csub(u, v);
         }
     }
     __syncthreads();
@@ -122,9 +166,8 @@ static __device__ void bluestein_inverse(double2 *x, int K, int M, const double2
 // Hermitian spectrum into a half-length complex FFT, transform, and write
 // f_{2n}, f_{2n+1} as the real and imaginary parts of z_n.  All threads of
 // the block take part; sm holds K (power of two) or M (Bluestein) entries.
-template <bool BLUE, bool CG>
-__device__ void phi_synth_ring(const PlanView &v, int ring, const double2 *qr, double *out_ring,
-                               double2 *sm)
+template <bool BLUE, class QAt>
+__device__ void phi_synth_ring_at(const PlanView &v, int ring, QAt qat, double *out_ring, double2 *sm)
 {
     const int L = v.lmax;
     const int J = v.ring_J[ring], K = J / 2, s = v.ring_s[ring];
@@ -132,8 +175,8 @@ __device__ void phi_synth_ring(const PlanView &v, int ring, const double2 *qr, d
     int logK = 0;
     while ((1 << logK) < K) ++logK;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double2 g0 = fold_G<CG>(qr, L, J, s, k);
-        double2 g1 = fold_G<CG>(qr, L, J, s, k + K);
+        const double2 g0 = fold_G(qat, L, J, s, k);
+        double2 g1 = fold_G(qat, L, J, s, k + K);
         if (s) g1 = times_i(g1);                           // e^{i pi K s / J} = i^s
         const double2 E = cadd(g0, g1), O = csub(g0, g1);
         double2 Zk = cadd(E, times_i(cmul(ring_root(T, J, 2LL * k), O)));
@@ -150,6 +193,35 @@ __device__ void phi_synth_ring(const PlanView &v, int ring, const double2 *qr, d
     double2 *out = reinterpret_cast<double2 *>(out_ring);
     for (int n = threadIdx.x; n < K; n += blockDim.x) out[n] = sm[n];
     __syncthreads();
+}
+
+// ... with q_m read from a ring-major array qr[m]
+template <bool BLUE, bool CG>
+__device__ void phi_synth_ring(const PlanView &v, int ring, const double2 *qr, double *out_ring,
+                               double2 *sm)
+{
+    phi_synth_ring_at<BLUE>(v, ring, [qr](int m) { return ldq<CG>(qr + m); }, out_ring, sm);
+}
+
+// ... with q_m formed from the two parity halves of the butterfly output,
+// stored map-major: qt[((b * 2 + t) * nhalf + r) * (L + 1) + m] (complex);
+// north rings (ring < nhalf) take q^0 + q^1, their mirrors q^0 - q^1.
+template <bool BLUE, bool CG>
+__device__ void phi_synth_ring_qt(const PlanView &v, int ring, const double2 *qt, int b,
+                                  double *out_ring, double2 *sm)
+{
+    const int Z = v.nhalf, L = v.lmax;
+    const bool north = ring < Z;
+    const int r = north ? ring : v.nrings - 1 - ring;
+    const double2 *q0 = qt + ((size_t)(b * 2) * Z + r) * (L + 1);
+    const double2 *q1 = q0 + (size_t)Z * (L + 1);
+    auto qat = [=](int m) {
+        const double2 x0 = ldq<CG>(q0 + m);
+        if (m + 1 > L) return x0;
+        const double2 x1 = ldq<CG>(q1 + m);
+        return north ? make_double2(x0.x + x1.x, x0.y + x1.y) : make_double2(x0.x - x1.x, x0.y - x1.y);
+    };
+    phi_synth_ring_at<BLUE>(v, ring, qat, out_ring, sm);
 }
 
 }  // namespace shtb_dev

@@ -10,6 +10,17 @@ pytestmark = pytest.mark.gpu
 import paper_1110_4874_gb300 as sh  # noqa: E402
 from paper_1110_4874_gb300 import synthetic  # noqa: E402
 
+# The batch kernel and the single-request path apply the same compressed
+# operator but sum in a different order (the batch combines the parity halves
+# in a separate pass and runs radix-2 ring FFTs; the single-request path
+# fuses the combine into radix-4 FFTs), so the maps agree to rounding, not
+# bit for bit: a few ulps of the largest pixel times log2 of the FFT length.
+REL = 1e-14
+
+
+def same_map(got, want):
+    return float((got - want).abs().max()) <= REL * float(want.abs().max())
+
 
 @pytest.fixture(scope="module")
 def setup():
@@ -34,6 +45,7 @@ def test_batch_equals_plain_requests(setup):
     info = sh.shtb_batch_info(batch)
     assert info["warps_per_block"] in (4, 8) and info["grid"] > 0 and info["npacks"] > 0
     torch.cuda.synchronize()
+    first = None
     for it in range(2):          # first run captures the graph, second replays it
         for _, _, maps in reqs:
             maps.fill_(float("nan"))
@@ -41,7 +53,11 @@ def test_batch_equals_plain_requests(setup):
         sh.shtb_batch_status(batch)
         for p, alm, maps in reqs:
             want = p.synthesize(alm)
-            assert torch.equal(maps, want), f"run {it}"
+            assert same_map(maps, want), f"run {it}"
+        if first is None:
+            first = [maps.clone() for _, _, maps in reqs]
+        else:            # the replay repeats the captured run bit for bit
+            assert all(torch.equal(a, m) for a, (_, _, m) in zip(first, reqs))
     sh.shtb_batch_destroy(batch)
 
 
@@ -53,7 +69,7 @@ def test_batch_on_a_user_stream(setup):
         sh.shtb_batch_run(batch, s)
     sh.shtb_batch_status(batch, s)
     for p, alm, maps in reqs[:4]:
-        assert torch.equal(maps, p.synthesize(alm))
+        assert same_map(maps, p.synthesize(alm))
     sh.shtb_batch_destroy(batch)
 
 
@@ -72,7 +88,7 @@ def test_batch_wait_timeout_reports_status(setup):
     sh.shtb_batch_run(batch)
     sh.shtb_batch_status(batch)
     for p, alm, maps in reqs[:3]:
-        assert torch.equal(maps, p.synthesize(alm))
+        assert same_map(maps, p.synthesize(alm))
     sh.shtb_batch_destroy(batch)
 
 
