@@ -47,53 +47,80 @@ __device__ __forceinline__ void qt_store(double *qt, long long e, int nhalf, int
     qt[((((long long)b * 2 + t) * nhalf + r) * (L + 1) + m) * 2 + (c & 1)] = v;
 }
 
-// u = R^T a over one residual block (lane tile over the block's k columns).
-// ai: [idx][nmaps] complex, the group's maps at b0 .. b0+NB-1.
+// Warp layout of the synthesis items: each lane owns ONE real component c of
+// the C = 2 x maps carried per entry, and the LD = 32 / C lanes that share a
+// component split the rows (level items) or columns (residual blocks) of the
+// item, so a pass wastes at most LD - 1 rows or columns (1 at 8 maps).
+template <int C>
+struct Lanes {
+    static_assert(C >= 2 && C <= 16 && 32 % C == 0, "2..16 real components per entry");
+    static constexpr int LD = 32 / C;    // lanes per component
+    static constexpr int NRMAX = C < 8 ? C : 8;   // residual columns per lane and pass
+};
+
+// NR columns per lane of one residual block, columns s0 + sl + r LD (r < NR):
+// u_s = sum_j R[j][s] a_j for component c, then stored to u (or q^t).
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_r_pass(const BfRItem &it, int L, int nhalf, const int *__restrict__ ints,
+                                          const double *__restrict__ R, const double *a0, int astride,
+                                          int s0, int sl, int c, double *ubuf, double *qt)
+{
+    constexpr int C = 2 * NB, LD = Lanes<C>::LD;
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    const int k = it.k;
+#pragma unroll 2
+    for (int j = 0; j < it.nrows; ++j) {
+        const double a = ldp<CG>(a0 + (size_t)j * astride);
+        const double *__restrict__ Rj = R + (size_t)j * k + s0 + sl;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const double t = s0 + sl + r * LD < k ? Rj[r * LD] : 0.0;
+            acc[r] = fma(t, a, acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int sidx = s0 + sl + r * LD;
+        if (sidx >= k) continue;
+        if (it.to_rings) qt_store(qt, ints[it.out_off + sidx], nhalf, L, c, acc[r]);
+        else ubuf[(size_t)(it.out_off + sidx) * C + c] = acc[r];
+    }
+}
+
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_r_dispatch(int nr, const BfRItem &it, int L, int nhalf, const int *ints,
+                                              const double *R, const double *a0, int astride, int s0, int sl,
+                                              int c, double *ubuf, double *qt)
+{
+    if constexpr (NR > 1) {
+        if (nr < NR) {
+            bf_r_dispatch<NB, NR - 1, CG>(nr, it, L, nhalf, ints, R, a0, astride, s0, sl, c, ubuf, qt);
+            return;
+        }
+    }
+    bf_r_pass<NB, NR, CG>(it, L, nhalf, ints, R, a0, astride, s0, sl, c, ubuf, qt);
+}
+
+// u = R^T a over one residual block.  ai: [idx][nmaps] complex, the group's
+// maps at b0 .. b0+NB-1; chain row j of (m, t) is a_{m+t+2j}.  A pass covers
+// up to LD x NRMAX columns; its per-lane column count is exact (the block's
+// columns rounded up to LD).
 template <int NB, bool CG>
 __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, int nhalf, const int *__restrict__ ints,
                                           const double *__restrict__ dbl, const double2 *ai, int nmaps,
                                           int b0, double *ubuf, double *qt, int lane)
 {
-    constexpr int C = 2 * NB;
-    using Tl = Tile<C>;
+    constexpr int C = 2 * NB, LD = Lanes<C>::LD;
     const double *__restrict__ R = dbl + it.data_off;
     const long long aoff = alm_off(L, it.m) + it.t;   // chain row j at aoff + 2j
-    const int sl = lane % Tl::LD, cg = lane / Tl::LD;
-    for (int s0 = 0; s0 < it.k; s0 += Tl::CH) {
-        double acc[Tl::RPL][Tl::CPL];
-#pragma unroll
-        for (int r = 0; r < Tl::RPL; ++r)
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) acc[r][c] = 0.0;
-#pragma unroll 2
-        for (int j = 0; j < it.nrows; ++j) {
-            const double *aj = reinterpret_cast<const double *>(
-                ai + (size_t)(aoff + 2 * (it.j0 + j)) * nmaps + b0) + cg * Tl::CPL;
-            double av[Tl::CPL];
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) av[c] = ldp<CG>(aj + c);
-#pragma unroll
-            for (int r = 0; r < Tl::RPL; ++r) {
-                const int sidx = s0 + sl + r * Tl::LD;
-                const double t = sidx < it.k ? R[(size_t)j * it.k + sidx] : 0.0;
-#pragma unroll
-                for (int c = 0; c < Tl::CPL; ++c) acc[r][c] = fma(t, av[c], acc[r][c]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < Tl::RPL; ++r) {
-            const int sidx = s0 + sl + r * Tl::LD;
-            if (sidx >= it.k) continue;
-            if (it.to_rings) {
-                const long long e = ints[it.out_off + sidx];
-#pragma unroll
-                for (int c = 0; c < Tl::CPL; ++c) qt_store(qt, e, nhalf, L, cg * Tl::CPL + c, acc[r][c]);
-            } else {
-                double *dst = ubuf + (size_t)(it.out_off + sidx) * C;
-#pragma unroll
-                for (int c = 0; c < Tl::CPL; ++c) dst[cg * Tl::CPL + c] = acc[r][c];
-            }
-        }
+    const int sl = lane % LD, c = lane / LD;
+    const double *a0 = reinterpret_cast<const double *>(ai + (size_t)(aoff + 2 * it.j0) * nmaps + b0) + c;
+    const int astride = 4 * nmaps;                    // doubles between chain rows j and j + 1
+    for (int s0 = 0; s0 < it.k; s0 += LD * Lanes<C>::NRMAX) {
+        const int nr = min(Lanes<C>::NRMAX, (it.k - s0 + LD - 1) / LD);
+        bf_r_dispatch<NB, Lanes<C>::NRMAX, CG>(nr, it, L, nhalf, ints, R, a0, astride, s0, sl, c, ubuf, qt);
     }
 }
 
@@ -107,78 +134,92 @@ __host__ __device__ constexpr int out_stride()
     return C + 1;
 }
 
+// NR dense rows per lane of one child, rows q0 + dl + r LD (r < NR): each a
+// k-long dot product of the child's T column with its u (component c); every
+// u value loaded serves the lane's NR rows.
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_dense_pass(int k, int nd, const double *__restrict__ T,
+                                              const int *__restrict__ dpos, const double *uc, int q0, int dl,
+                                              int c, double *out)
+{
+    constexpr int C = 2 * NB, LD = Lanes<C>::LD, OS = out_stride<C>();
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    const double *__restrict__ Tq = T + q0 + dl;
+#pragma unroll 2
+    for (int i = 0; i < k; ++i) {
+        const double uv = ldp<CG>(uc + (size_t)i * C);
+        const double *__restrict__ Ti = Tq + (size_t)i * nd;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const double t = q0 + dl + r * LD < nd ? Ti[r * LD] : 0.0;
+            acc[r] = fma(t, uv, acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int d = q0 + dl + r * LD;
+        if (d < nd) out[dpos[d] * OS + c] += acc[r];
+    }
+}
+
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_dense_dispatch(int nr, int k, int nd, const double *T, const int *dpos,
+                                                  const double *uc, int q0, int dl, int c, double *out)
+{
+    if constexpr (NR > 1) {
+        if (nr < NR) {
+            bf_dense_dispatch<NB, NR - 1, CG>(nr, k, nd, T, dpos, uc, q0, dl, c, out);
+            return;
+        }
+    }
+    bf_dense_pass<NB, NR, CG>(k, nd, T, dpos, uc, q0, dl, c, out);
+}
+
+// Each child in turn: its dense rows (passes of up to LD x NRMAX rows, the
+// per-lane row count exact), then its identity entries.  A child's dense and
+// identity positions are distinct, so lanes never update the same scratch
+// entry within a child; the warp syncs between the children, whose positions
+// may coincide.
 template <int NB, bool CG>
 __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
                                               const double *__restrict__ dbl, const double *uin,
                                               double *uout, double *qt, double *out, int lane)
 {
-    constexpr int C = 2 * NB;
+    constexpr int C = 2 * NB, LD = Lanes<C>::LD, NRMAX = Lanes<C>::NRMAX;
     constexpr int OS = out_stride<C>();
-    using Tl = Tile<C>;
     for (int i = lane; i < it.nc * OS; i += 32) out[i] = 0.0;
     __syncwarp();
-    // dense parts of both children as one list of nd0 + nd1 rows (LD rows per
-    // pass), each row a k-long dot product with its child's u; the top child's
-    // rows are added before the bottom child's, so two rows that hit the same
-    // candidate never update it at the same time
-    const int dl = lane % Tl::LD, cg = lane / Tl::LD;
-    const int nd0 = it.nd[0], ndt = it.nd[0] + it.nd[1];
-    const int kmax = max(it.k[0], it.k[1]);
-    for (int q0 = 0; q0 < ndt; q0 += Tl::LD) {
-        const int q = q0 + dl;
-        const bool valid = q < ndt;
-        const int s = (valid && q >= nd0) ? 1 : 0;
-        const int d = s ? q - nd0 : (valid ? q : 0);
-        const int k = s ? it.k[1] : it.k[0], nd = s ? it.nd[1] : it.nd[0];
-        const double *u = uin + (size_t)(s ? it.u_off[1] : it.u_off[0]) * C + cg * Tl::CPL;
-        const double *__restrict__ T = dbl + (s ? it.T_off[1] : it.T_off[0]) + d;
-        double acc[Tl::CPL];
+    const int dl = lane % LD, c = lane / LD;
 #pragma unroll
-        for (int c = 0; c < Tl::CPL; ++c) acc[c] = 0.0;
-#pragma unroll 4
-        for (int i = 0; i < kmax; ++i) {
-            const bool live = valid && i < k;
-            const double t = live ? T[(size_t)i * nd] : 0.0;
-            const double *ui = u + (size_t)(live ? i : 0) * C;
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) acc[c] = fma(t, ldp<CG>(ui + c), acc[c]);
-        }
-        double *o = out + (valid ? ints[(s ? it.dpos_off[1] : it.dpos_off[0]) + d] : 0) * OS + cg * Tl::CPL;
-        if (valid && s == 0) {
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) o[c] += acc[c];
-        }
-        __syncwarp();
-        if (valid && s == 1) {
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) o[c] += acc[c];
-        }
-        __syncwarp();
-    }
-    // identity parts: out[skeleton position] += u (top child, then bottom)
     for (int s = 0; s < 2; ++s) {
-        const int k = s ? it.k[1] : it.k[0];
-        const double *u = uin + (size_t)(s ? it.u_off[1] : it.u_off[0]) * C;
-        const int *__restrict__ ipos = ints + (s ? it.ipos_off[1] : it.ipos_off[0]);
-        for (int i = lane; i < k; i += 32) {
-            double *o = out + ipos[i] * OS;
-            const double *ui = u + (size_t)i * C;
-#pragma unroll
-            for (int c = 0; c < C; ++c) o[c] += ldp<CG>(ui + c);
+        const int k = it.k[s], nd = it.nd[s];
+        const double *u = uin + (size_t)it.u_off[s] * C;
+        const double *__restrict__ T = dbl + it.T_off[s];
+        const int *__restrict__ dpos = ints + it.dpos_off[s];
+        for (int q0 = 0; q0 < nd; q0 += LD * NRMAX) {
+            const int nr = min(NRMAX, (nd - q0 + LD - 1) / LD);
+            bf_dense_dispatch<NB, NRMAX, CG>(nr, k, nd, T, dpos, u + c, q0, dl, c, out);
+        }
+        const int *__restrict__ ipos = ints + it.ipos_off[s];
+        for (int x = lane; x < k * C; x += 32) {
+            const int i = x / C, cc = x - i * C;
+            out[ipos[i] * OS + cc] += ldp<CG>(u + x);
         }
         __syncwarp();
     }
     if (it.to_rings) {
         const int *__restrict__ ent = ints + it.out_off;
         for (int i = lane; i < it.nc * C; i += 32) {
-            const int c = i / it.nc, cpos = i - c * it.nc;
-            qt_store(qt, ent[cpos], nhalf, L, c, out[cpos * OS + c]);
+            const int cc = i / it.nc, cpos = i - cc * it.nc;
+            qt_store(qt, ent[cpos], nhalf, L, cc, out[cpos * OS + cc]);
         }
     } else {
         double *dst = uout + (size_t)it.out_off * C;
         for (int i = lane; i < it.nc * C; i += 32) {
-            const int cpos = i / C, c = i - cpos * C;
-            dst[i] = out[cpos * OS + c];
+            const int cpos = i / C, cc = i - cpos * C;
+            dst[i] = out[cpos * OS + cc];
         }
     }
     __syncwarp();
