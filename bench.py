@@ -43,14 +43,31 @@ UNIT = "ms/map"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM traffic of the dominant kernel from an ncu capture (see profiles/),
-# per kernel; valid only while that kernel's source file is unchanged.
+# in the unit `achieved` is computed over (the kernel's launches of one step);
+# valid only while the kernel's source files are unchanged.
 NCU_TRAFFIC = {
     "legendre_synth_kernel": {
-        "source": "paper_1110_4874_gb300/csrc/shtb_legendre.cu",
-        "source_sha256": "2716a9eb2679dc0a7730c490c671b800e69d7688a7fb6465ffbe4592e8d7cacb",
+        "sources": ["paper_1110_4874_gb300/csrc/shtb_legendre.cu"],
+        "sha256": "2716a9eb2679dc0a7730c490c671b800e69d7688a7fb6465ffbe4592e8d7cacb",
         # 410.5 MB measured at Nside=512, L=1024; every array scales with Nside*L (x16)
-        "bytes_per_launch": 16 * 410_475_008,
+        "bytes": 16 * 410_475_008,
         "profile": "profiles/legendre_synth_nside512_l1024_b8.md",
+    },
+    # butterfly kernels: DRAM bytes of all launches of one synthesis of 8 maps at
+    # Nside=2048, L=4096 (1-pass ncu capture of the full workload)
+    "bf_level_kernel": {
+        "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu",
+                    "paper_1110_4874_gb300/csrc/shtb_butterfly.h"],
+        "sha256": "7e540cf29d2bbc52d493395ee7c670534a3856ade2ffe69af3035708131528ba",
+        "bytes": 61_850_000_000 + 24_940_000_000,     # read + write over the 6 level launches
+        "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
+    },
+    "bf_r_kernel": {
+        "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu",
+                    "paper_1110_4874_gb300/csrc/shtb_butterfly.h"],
+        "sha256": "7e540cf29d2bbc52d493395ee7c670534a3856ade2ffe69af3035708131528ba",
+        "bytes": 10_720_000_000 + 3_640_000_000,
+        "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
 }
 
@@ -66,6 +83,17 @@ def measured_peaks():
 def file_sha256(path):
     with open(os.path.join(ROOT, path), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()
+
+
+def sources_sha256(paths):
+    """One digest over several source files (a single file: its own sha256)."""
+    if len(paths) == 1:
+        return file_sha256(paths[0])
+    h = hashlib.sha256()
+    for path in paths:
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 # ------------------------------------------------------------ clock sampling
@@ -266,8 +294,8 @@ def run_ours(args, rank, world, dist):
     achieved = flops / (kms * 1e-3) / 1e12
     traffic = None
     rec = NCU_TRAFFIC.get(kname)
-    if rec and rec["bytes_per_launch"] and rec["source_sha256"] == file_sha256(rec["source"]):
-        traffic = rec["bytes_per_launch"]
+    if rec and rec["bytes"] and rec["sha256"] == sources_sha256(rec["sources"]):
+        traffic = rec["bytes"]
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "kernel": f"{kname} (FP64 pipe)",
