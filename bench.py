@@ -58,14 +58,14 @@ NCU_TRAFFIC = {
     "bf_level_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.h"],
-        "sha256": "7e540cf29d2bbc52d493395ee7c670534a3856ade2ffe69af3035708131528ba",
+        "sha256": "d107543be69049449cd86cea14dabbd53c10e1448ae0840a079ac7e46460faf5",
         "bytes": 61_850_000_000 + 24_940_000_000,     # read + write over the 6 level launches
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
     "bf_r_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.h"],
-        "sha256": "7e540cf29d2bbc52d493395ee7c670534a3856ade2ffe69af3035708131528ba",
+        "sha256": "d107543be69049449cd86cea14dabbd53c10e1448ae0840a079ac7e46460faf5",
         "bytes": 10_720_000_000 + 3_640_000_000,
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },

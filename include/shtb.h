@@ -272,6 +272,16 @@ int shtb_measure_fp64_peak(int device, double *dfma_gflops, double *dmma_gflops)
 /* Legendre stage only: q_m(z_k) for every ring (Eq. legendre-transform). */
 int shtb_test_legendre(shtb_plan plan, const double *alm_dev, double *q_dev, int nmaps,
                        void *stream);
+/* Compressed Legendre stage only (Sec. 3.2, Eq. factor-into-block-diagonal):
+   residual blocks and butterfly levels of a compressed plan (eps > 0), giving
+   the two parity halves q^t_m(z_r) = sum_j a_{m+t+2j,m} Ptilde_{m+t+2j}^m(z_r)
+   (t = 0, 1) at the 2 nside half-rings r with z_r >= 0, north to the equator.
+   qt_dev: device, [nmaps][2][2 nside][lmax+1] complex128 (written; the empty
+   chain t = 1, m = lmax is 0).  The maps are q^0 + q^1 on ring r and
+   q^0 - q^1 on its mirror (Eq. q-even-odd2).  Errors: SHTB_ENOTSUP for an
+   uncompressed plan, as shtb_synthesize otherwise. */
+int shtb_test_butterfly(shtb_plan plan, const double *alm_dev, double *qt_dev, int nmaps,
+                        void *stream);
 /* Ring stage only: pixels from q (Eq. sh-baseline, Eq. phi, Eq. tau). */
 int shtb_test_phi(shtb_plan plan, const double *q_dev, double *map_dev, int nmaps,
                   void *stream);

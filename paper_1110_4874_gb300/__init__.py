@@ -96,6 +96,7 @@ SIGNATURES = {
     "shtb_profile_read": (_I, [_P, _DP, _I, ctypes.POINTER(_I)]),
     "shtb_measure_fp64_peak": (_I, [_I, _DP, _DP]),
     "shtb_test_legendre": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_test_butterfly": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_phi": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_phi_adjoint": (_I, [_P, _P, _P, _I, _P]),
     "shtb_test_legendre_adjoint": (_I, [_P, _P, _P, _I, _P]),
@@ -278,6 +279,12 @@ def shtb_measure_fp64_peak(device: int = 0) -> tuple[float, float]:
 def shtb_test_legendre(plan, alm, q, nmaps: int, stream=None) -> None:
     import torch
     _call_dev("shtb_test_legendre", plan, alm, torch.complex128, q, torch.complex128, nmaps, stream)
+
+
+def shtb_test_butterfly(plan, alm, qt, nmaps: int, stream=None) -> None:
+    """Compressed Legendre stage: qt complex128 [nmaps, 2, 2 nside, lmax+1]."""
+    import torch
+    _call_dev("shtb_test_butterfly", plan, alm, torch.complex128, qt, torch.complex128, nmaps, stream)
 
 
 def shtb_test_phi(plan, q, maps, nmaps: int, stream=None) -> None:

@@ -400,6 +400,19 @@ int shtb_test_legendre(shtb_plan p, const double *alm_dev, double *q_dev, int nm
     return launch_legendre_synth(p, w.ap, (double2 *)q_dev, nmaps, st);
 }
 
+int shtb_test_butterfly(shtb_plan p, const double *alm_dev, double *qt_dev, int nmaps, void *stream)
+{
+    int rc = check_call(p, alm_dev, qt_dev, nmaps);
+    if (rc) return rc;
+    if (!p->bf) return shtb_fail(SHTB_ENOTSUP, "shtb_test_butterfly needs a compressed plan (eps > 0)");
+    if ((rc = ensure_ws(p, nmaps))) return rc;
+    Workspace w = carve(p, nmaps);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the (m = L, t = 1) chain is empty: its entries stay zero
+    SHTB_CUDA_TRY(cudaMemsetAsync(qt_dev, 0, sizeof(double2) * 2 * (size_t)nmaps * p->nhalf * (p->lmax + 1), st));
+    return launch_bf_synth(p, (const double2 *)alm_dev, w.ap, w.bf, nullptr, nmaps, st, qt_dev);
+}
+
 int shtb_test_phi(shtb_plan p, const double *q_dev, double *map_dev, int nmaps, void *stream)
 {
     int rc = check_call(p, q_dev, map_dev, nmaps);

@@ -73,6 +73,9 @@ bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, 
                                        sout + (size_t)wib * maxnc * OS, lane);
 }
 
+// One map group: residual blocks, butterfly levels, then (map != nullptr)
+// the ring stage.  With map == nullptr the group's q^t is the caller's
+// array (the Legendre stage alone).
 template <int NB>
 int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
               double *qt, double *map, cudaStream_t st)
@@ -109,6 +112,7 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
     }
     profile_end(pp, st, 6, ev);
     profile_end(pp, st, 0, ev_leg);
+    if (!map) return SHTB_OK;
     // ring stage of this group straight from q^0, q^1 (parity combine fused)
     ev = profile_begin(pp, st);
     int rc = launch_phi_synth_qt(p, qt, NB, map, b0, st);
@@ -289,13 +293,16 @@ size_t bf_workspace_bytes(const shtb_plan_s *p)
 }
 
 int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
-                    int nmaps, cudaStream_t st)
+                    int nmaps, cudaStream_t st, double *qt_out)
 {
     const BfPlanDev &bf = *p->bf;
     const size_t entry = 16;
     double *u0 = (double *)ws;
     double *u1 = u0 + (size_t)bf.u_entries * entry;
-    double *qt = u1 + (size_t)bf.u_entries * entry;
+    double *qt_ws = u1 + (size_t)bf.u_entries * entry;
+    // q^t of map b in the caller's [nmaps][2][nhalf][L+1] array (Legendre stage alone)
+    const size_t qt_map = (size_t)4 * p->nhalf * (p->lmax + 1);
+    auto qt_of = [&](int b0) { return qt_out ? qt_out + (size_t)b0 * qt_map : qt_ws; };
     const int ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
     bf_interleave_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ai, nmaps);
     SHTB_CUDA_TRY(cudaGetLastError());
@@ -304,6 +311,7 @@ int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void 
     for (int b0 = 0; b0 < nmaps;) {
         const int left = nmaps - b0;
         int rc;
+        double *qt = qt_of(b0);
         if (left >= 8) { rc = run_group<8>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 8; }
         else if (left >= 4) { rc = run_group<4>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 4; }
         else if (left >= 2) { rc = run_group<2>(p, ai, nmaps, b0, u0, u1, qt, map, st); b0 += 2; }

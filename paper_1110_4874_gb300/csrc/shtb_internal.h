@@ -69,10 +69,26 @@ struct PlanView {
     const long long *ring_start;     // first pixel of each ring
     const long long *ring_tw;        // offset of the ring's e^{i pi n / J} table in tw
     const double2 *tw;
-    const int *ring_M;               // Bluestein length (0 = power-of-two ring)
-    const long long *ring_fb;        // offset of the ring's Bluestein filter in fb
+    // mixed-radix transforms (the stand-alone ring kernels): per ring the
+    // radix list {n, r_0 .. r_{n-1}} (rad + ring_rad[ring]) of its transform
+    // length -- K = J/2 when K factors over 2, 3, 5, 7, 11, 13 (ring_mx = 0),
+    // else the Bluestein length ring_mx (smooth, >= 2K - 1) with the filter
+    // at mfb + ring_mfb (position order, scaled by 1/ring_mx) and the
+    // e^{2 pi i t / ring_mx} table at mtw + ring_mtw
+    const int *ring_rad;
+    const int *rad;
+    const int *ring_mx;
+    const long long *ring_mfb;
+    const double2 *mfb;
+    const long long *ring_mtw;
+    const double2 *mtw;
+    // radix-2 tables of the persistent batch kernel: Bluestein length
+    // (0 = power-of-two ring), filter offset in fb (bit-reversed order),
+    // e^{2 pi i n / Wlen}
+    const int *ring_M;
+    const long long *ring_fb;
     const double2 *fb;
-    const double2 *W;                // e^{2 pi i n / Wlen}, n < Wlen
+    const double2 *W;
     int Wlen;
 };
 
@@ -90,10 +106,15 @@ struct shtb_plan_s {
     std::vector<int> ring_J, ring_s, ring_M;
     std::vector<long long> ring_start;
 
-    // ring lists for the two FFT kernels
-    std::vector<int> pow2_rings, blue_rings;
+    // ring lists of the three ring-kernel variants (mixed radix: direct
+    // transform of length K over radices 2..7, Bluestein, direct with a
+    // radix 11 or 13), heaviest rings first
+    std::vector<int> direct_rings, blue_rings, big_rings;
+    int max_K_direct = 0, max_M_mx = 0, max_K_big = 0;
+    int *d_direct_rings = nullptr, *d_blue_rings = nullptr, *d_big_rings = nullptr;
+    // largest radix-2 transform of the batch kernel (power-of-two K, or the
+    // power-of-two Bluestein length)
     int max_K_pow2 = 0, max_M_blue = 0;
-    int *d_pow2_rings = nullptr, *d_blue_rings = nullptr;
 
     // device allocations owned by the plan (freed in destroy)
     std::vector<void *> allocations;
@@ -156,8 +177,10 @@ int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *
 
 // shtb_butterfly.cu
 size_t bf_workspace_bytes(const shtb_plan_s *p);
+// map != nullptr: the whole synthesis; map == nullptr: the Legendre stage
+// alone, q^t of map b written to qt_out + b [2][nhalf][L+1] complex
 int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
-                    int nmaps, cudaStream_t st);
+                    int nmaps, cudaStream_t st, double *qt_out = nullptr);
 void bf_release(shtb_plan_s *p);
 int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
                       int nmaps, cudaStream_t st);

@@ -10,11 +10,12 @@
 // of length K: Z_k = E_k + i e^{2 pi i k/J} O_k with E_k = g_k + g_{k+K},
 // O_k = g_k - g_{k+K}; then z_n = sum_k Z_k e^{2 pi i k n / K} holds the
 // pixels as f_{2n} + i f_{2n+1}.
-// One CTA per (ring, map); the ring's data live in shared memory.  K a power
-// of two: in-place radix-2 FFT from bit-reversed input.  Otherwise Bluestein's
-// chirp transform through a power-of-two convolution of length M >= 2K-1
-// (decimation in frequency, pointwise product with a precomputed filter in
-// bit-reversed order, decimation in time), so no permutation pass is needed.
+// One CTA per (ring, map); the ring's data live in shared memory.  K factoring
+// over 2, 3, 5, 7, 11, 13: in-place mixed-radix FFT (radices 4, 2, 3, 5, 7,
+// 11, 13) from position-order input.  Otherwise Bluestein's chirp transform
+// through a convolution of 7-smooth length M >= 2K-1 (decimation in
+// frequency, pointwise product with a precomputed filter in position order,
+// decimation in time), so no permutation pass is needed.
 #include <cuda_runtime.h>
 
 #include "shtb_internal.h"
@@ -26,7 +27,7 @@ using namespace shtb_dev;
 
 constexpr int kPhiThreads = 256;
 
-template <bool BLUE>
+template <int KIND>
 __global__ void __launch_bounds__(kPhiThreads)
 phi_synth_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ q,
                  double *__restrict__ map)
@@ -34,13 +35,13 @@ phi_synth_kernel(PlanView v, const int *__restrict__ rings, const double2 *__res
     extern __shared__ double2 sm[];
     const int ring = rings[blockIdx.x];
     const int b = blockIdx.y;
-    shtb_dev::phi_synth_ring<BLUE, false>(v, ring, q + ((size_t)b * v.nrings + ring) * (v.lmax + 1),
+    shtb_dev::phi_synth_ring<KIND, false>(v, ring, q + ((size_t)b * v.nrings + ring) * (v.lmax + 1),
                                           map + (size_t)b * v.npix + v.ring_start[ring], sm);
 }
 
 // ring stage of a compressed plan's map group, straight from the parity
 // halves q^0, q^1 of the butterfly output (no separate combine pass)
-template <bool BLUE>
+template <int KIND>
 __global__ void __launch_bounds__(kPhiThreads)
 phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ qt,
                     double *__restrict__ map, int b0)
@@ -48,23 +49,23 @@ phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__
     extern __shared__ double2 sm[];
     const int ring = rings[blockIdx.x];
     const int b = blockIdx.y;
-    shtb_dev::phi_synth_ring_qt<BLUE, false>(v, ring, qt, b,
+    shtb_dev::phi_synth_ring_qt<KIND, false>(v, ring, qt, b,
                                              map + (size_t)(b0 + b) * v.npix + v.ring_start[ring], sm);
 }
 
-template <bool BLUE>
+template <int KIND>
 __global__ void __launch_bounds__(kPhiThreads)
 phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__restrict__ map,
                    double2 *__restrict__ qa)
 {
+    constexpr bool BLUE = KIND == kBluestein;
     extern __shared__ double2 sm[];
     const int ring = rings[blockIdx.x];
     const int b = blockIdx.y;
     const int L = v.lmax;
     const int J = v.ring_J[ring], K = J / 2, s = v.ring_s[ring];
     const double2 *__restrict__ T = v.tw + v.ring_tw[ring];
-    int logK = 0;
-    while ((1 << logK) < K) ++logK;
+    const int *__restrict__ rl = v.rad + v.ring_rad[ring];
 
     // z_n = f_{2n} + i f_{2n+1}; forward DFT Zf_k = sum_n z_n e^{-2 pi i k n/K}
     const double2 *in = reinterpret_cast<const double2 *>(map + (size_t)b * v.npix + v.ring_start[ring]);
@@ -74,11 +75,11 @@ phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__re
     }
     if (BLUE) {
         __syncthreads();
-        bluestein_inverse(sm, K, v.ring_M[ring], T, v.fb + v.ring_fb[ring], v.W, v.Wlen);
+        bluestein_mx(sm, K, v.ring_mx[ring], T, v.mfb + v.ring_mfb[ring], rl, TwTable{v.mtw + v.ring_mtw[ring]});
         for (int n = threadIdx.x; n < K; n += blockDim.x) sm[n] = cconj(sm[n]);
         __syncthreads();
     } else {
-        fft_dif_forward(sm, K, v.W, v.Wlen);   // bit-reversed order
+        fft_mx_dif<KIND == kDirectBig>(sm, K, rl, TwRing{T, J});   // position order
     }
 
     // F_r = E'_r + e^{-2 pi i r/J} O'_r with E' = (Zf_r + conj Zf_{K-r})/2,
@@ -89,8 +90,8 @@ phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__re
         const int r = m % J;
         const int rho = r < K ? r : r - K;
         const int rho2 = rho == 0 ? 0 : K - rho;
-        const double2 A = BLUE ? sm[rho] : sm[bitrev(rho, logK)];
-        const double2 B = cconj(BLUE ? sm[rho2] : sm[bitrev(rho2, logK)]);
+        const double2 A = BLUE ? sm[rho] : sm[fft_pos(rho, K, rl)];
+        const double2 B = cconj(BLUE ? sm[rho2] : sm[fft_pos(rho2, K, rl)]);
         const double2 Ep = make_double2(0.5 * (A.x + B.x), 0.5 * (A.y + B.y));
         const double2 D = make_double2(0.5 * (A.x - B.x), 0.5 * (A.y - B.y));   // (A - B)/2
         const double2 Op = make_double2(D.y, -D.x);                             // D / i
@@ -99,43 +100,65 @@ phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__re
     }
 }
 
+// one launch per ring kind: grid (rings of that kind) x maps, shared memory
+// for the kind's longest transform
+struct RingSet {
+    const int *rings;
+    size_t n;
+    int len;
+};
+
+RingSet ring_set(const shtb_plan_s *p, int kind)
+{
+    if (kind == kDirect) return {p->d_direct_rings, p->direct_rings.size(), p->max_K_direct};
+    if (kind == kBluestein) return {p->d_blue_rings, p->blue_rings.size(), p->max_M_mx};
+    return {p->d_big_rings, p->big_rings.size(), p->max_K_big};
+}
+
+template <int KIND>
+int launch_kind(const shtb_plan_s *p, bool synth, const void *in, void *out, int nmaps, cudaStream_t st)
+{
+    const RingSet rs = ring_set(p, KIND);
+    if (rs.n == 0) return SHTB_OK;
+    const size_t smem = sizeof(double2) * (size_t)rs.len;
+    const dim3 grid((unsigned)rs.n, (unsigned)nmaps);
+    if (synth) {
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        phi_synth_kernel<KIND><<<grid, kPhiThreads, smem, st>>>(p->view, rs.rings, (const double2 *)in,
+                                                                (double *)out);
+    } else {
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_adjoint_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+        phi_adjoint_kernel<KIND><<<grid, kPhiThreads, smem, st>>>(p->view, rs.rings, (const double *)in,
+                                                                  (double2 *)out);
+    }
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    return SHTB_OK;
+}
+
 int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int nmaps,
                cudaStream_t st)
 {
-    if (!p->pow2_rings.empty()) {
-        const size_t smem = sizeof(double2) * (size_t)p->max_K_pow2;
-        const dim3 grid((unsigned)p->pow2_rings.size(), (unsigned)nmaps);
-        if (synth) {
-            SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_kernel<false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            phi_synth_kernel<false><<<grid, kPhiThreads, smem, st>>>(
-                p->view, p->d_pow2_rings, (const double2 *)in, (double *)out);
-        } else {
-            SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_adjoint_kernel<false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            phi_adjoint_kernel<false><<<grid, kPhiThreads, smem, st>>>(
-                p->view, p->d_pow2_rings, (const double *)in, (double2 *)out);
-        }
-        SHTB_CUDA_TRY(cudaGetLastError());
-        ++p->launches;
-    }
-    if (!p->blue_rings.empty()) {
-        const size_t smem = sizeof(double2) * (size_t)p->max_M_blue;
-        const dim3 grid((unsigned)p->blue_rings.size(), (unsigned)nmaps);
-        if (synth) {
-            SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_kernel<true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            phi_synth_kernel<true><<<grid, kPhiThreads, smem, st>>>(
-                p->view, p->d_blue_rings, (const double2 *)in, (double *)out);
-        } else {
-            SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_adjoint_kernel<true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            phi_adjoint_kernel<true><<<grid, kPhiThreads, smem, st>>>(
-                p->view, p->d_blue_rings, (const double *)in, (double2 *)out);
-        }
-        SHTB_CUDA_TRY(cudaGetLastError());
-        ++p->launches;
-    }
+    int rc;
+    if ((rc = launch_kind<kBluestein>(p, synth, in, out, nmaps, st))) return rc;
+    if ((rc = launch_kind<kDirect>(p, synth, in, out, nmaps, st))) return rc;
+    return launch_kind<kDirectBig>(p, synth, in, out, nmaps, st);
+}
+
+template <int KIND>
+int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, double *map, int b0, cudaStream_t st)
+{
+    const RingSet rs = ring_set(p, KIND);
+    if (rs.n == 0) return SHTB_OK;
+    const size_t smem = sizeof(double2) * (size_t)rs.len;
+    SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    phi_synth_qt_kernel<KIND><<<dim3((unsigned)rs.n, (unsigned)nb), kPhiThreads, smem, st>>>(p->view, rs.rings,
+                                                                                            qt, map, b0);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
     return SHTB_OK;
 }
 
@@ -145,25 +168,10 @@ int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *
                         cudaStream_t st)
 {
     const double2 *q2 = (const double2 *)qt;
-    if (!p->pow2_rings.empty()) {
-        const size_t smem = sizeof(double2) * (size_t)p->max_K_pow2;
-        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        phi_synth_qt_kernel<false><<<dim3((unsigned)p->pow2_rings.size(), (unsigned)nb), kPhiThreads,
-                                     smem, st>>>(p->view, p->d_pow2_rings, q2, map, b0);
-        SHTB_CUDA_TRY(cudaGetLastError());
-        ++p->launches;
-    }
-    if (!p->blue_rings.empty()) {
-        const size_t smem = sizeof(double2) * (size_t)p->max_M_blue;
-        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        phi_synth_qt_kernel<true><<<dim3((unsigned)p->blue_rings.size(), (unsigned)nb), kPhiThreads,
-                                    smem, st>>>(p->view, p->d_blue_rings, q2, map, b0);
-        SHTB_CUDA_TRY(cudaGetLastError());
-        ++p->launches;
-    }
-    return SHTB_OK;
+    int rc;
+    if ((rc = launch_qt_kind<kBluestein>(p, q2, nb, map, b0, st))) return rc;
+    if ((rc = launch_qt_kind<kDirect>(p, q2, nb, map, b0, st))) return rc;
+    return launch_qt_kind<kDirectBig>(p, q2, nb, map, b0, st);
 }
 
 int launch_phi_synth(const shtb_plan_s *p, const double2 *q, double *map, int nmaps, cudaStream_t st)

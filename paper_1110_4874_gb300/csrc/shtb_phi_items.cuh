@@ -1,7 +1,7 @@
 // Device bodies of the ring stage (Eq. sh-baseline, Eq. tau): complex
-// helpers, the radix-4 and Bluestein FFTs in shared memory and the per-ring
-// synthesis used by the ring kernels of shtb_phi.cu (the persistent batch
-// kernel keeps its own copies, shtb_batch_items.cuh).
+// helpers, the mixed-radix and Bluestein FFTs in shared memory and the
+// per-ring synthesis used by the ring kernels of shtb_phi.cu (the persistent
+// batch kernel keeps its own radix-2 copies, shtb_batch_items.cuh).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -59,105 +59,235 @@ __device__ double2 fold_G(QAt qat, int L, int J, int s, int r)
     return acc;
 }
 
-__device__ __forceinline__ double2 times_mi(double2 a) { return make_double2(a.y, -a.x); }
+// ------------------------------------------------ mixed-radix ring FFTs
+// A transform of length N = r_0 r_1 ... r_{n-1} (radices 2, 3, 4, 5, 7, 11,
+// 13; list rl = {n, r_0, .., r_{n-1}}) runs in place in shared memory in n
+// passes.  Pass i works on blocks of B_i = N / (r_0 .. r_{i-1}) points and
+// combines the r_i points base + q N_i (N_i = B_i / r_i, q < r_i) of each of
+// its B_i / r_i butterflies.  Decimation in frequency (exponent -1, passes
+// 0..n-1: radix-r DFT, then the twiddles w_{B_i}^{-p j}) takes natural order
+// to "position" order, in which X_k, k = p_0 + r_0 (p_1 + r_1 (p_2 + ..)),
+// sits at pos(k) = sum_i p_i N_i.  Decimation in time (exponent +1, passes
+// n-1..0, twiddles first) is its conjugate transpose: position order in,
+// natural order out, unnormalised.  So no permutation pass is ever needed:
+// the fold writes straight to pos(k), and a Bluestein filter is stored in
+// position order.
 
-__device__ __forceinline__ int ilog2(int m)
+// e^{2 pi i k / R} for the odd radices, k < R: R = 3, 5, 7, 11, 13 at offsets
+// 0, 3, 8, 15, 26
+static __constant__ double kRootCos[39] = {
+    1.00000000000000000e+00, -5.00000000000000000e-01, -5.00000000000000000e-01,
+    1.00000000000000000e+00, 3.09016994374947451e-01, -8.09016994374947451e-01, -8.09016994374947451e-01,
+    3.09016994374947451e-01,
+    1.00000000000000000e+00, 6.23489801858733483e-01, -2.22520933956314393e-01, -9.00968867902419146e-01,
+    -9.00968867902419146e-01, -2.22520933956314393e-01, 6.23489801858733483e-01,
+    1.00000000000000000e+00, 8.41253532831181206e-01, 4.15415013001886435e-01, -1.42314838273285144e-01,
+    -6.54860733945285101e-01, -9.59492973614497369e-01, -9.59492973614497369e-01, -6.54860733945285101e-01,
+    -1.42314838273285144e-01, 4.15415013001886435e-01, 8.41253532831181206e-01,
+    1.00000000000000000e+00, 8.85456025653209911e-01, 5.68064746731155812e-01, 1.20536680255323048e-01,
+    -3.54604887042535621e-01, -7.48510748171101081e-01, -9.70941817426052012e-01, -9.70941817426052012e-01,
+    -7.48510748171101081e-01, -3.54604887042535621e-01, 1.20536680255323048e-01, 5.68064746731155812e-01,
+    8.85456025653209911e-01};
+static __constant__ double kRootSin[39] = {
+    0.00000000000000000e+00, 8.66025403784438597e-01, -8.66025403784438597e-01,
+    0.00000000000000000e+00, 9.51056516295153531e-01, 5.87785252292473137e-01, -5.87785252292473137e-01,
+    -9.51056516295153531e-01,
+    0.00000000000000000e+00, 7.81831482468029804e-01, 9.74927912181823619e-01, 4.33883739117558120e-01,
+    -4.33883739117558120e-01, -9.74927912181823619e-01, -7.81831482468029804e-01,
+    0.00000000000000000e+00, 5.40640817455597555e-01, 9.09631995354518330e-01, 9.89821441880932684e-01,
+    7.55749574354258269e-01, 2.81732556841429671e-01, -2.81732556841429671e-01, -7.55749574354258269e-01,
+    -9.89821441880932684e-01, -9.09631995354518330e-01, -5.40640817455597555e-01,
+    0.00000000000000000e+00, 4.64723172043768562e-01, 8.22983865893656352e-01, 9.92708874098053973e-01,
+    9.35016242685414833e-01, 6.63122658240795193e-01, 2.39315664287557767e-01, -2.39315664287557767e-01,
+    -6.63122658240795193e-01, -9.35016242685414833e-01, -9.92708874098053973e-01, -8.22983865893656352e-01,
+    -4.64723172043768562e-01};
+
+template <int R>
+__device__ __forceinline__ constexpr int root_off()
 {
-    return 31 - __clz(m);
+    return R == 3 ? 0 : R == 5 ? 3 : R == 7 ? 8 : R == 11 ? 15 : 26;
 }
 
-// Decimation in time, positive exponent: bit-reversed in, natural out.
-// Radix-4 passes, each fusing the radix-2 stages of half-size h and 2h: with
-// t1 = W^{2j} b, t2 = W^{j} c, t3 = W^{3j} d (W the 4h-th root),
-//   a' = (a+t1) + (t2+t3),  b' = (a-t1) + i (t2-t3),
-//   c' = (a+t1) - (t2+t3),  d' = (a-t1) - i (t2-t3);
-// an odd number of stages starts with one twiddle-free radix-2 pass.
-static __device__ void fft_dit_inverse(double2 *x, int M, const double2 *__restrict__ W, int Wlen)
+// y_q = sum_p a_p e^{S 2 pi i p q / R}, in place (S = +1 or -1)
+template <int R, int S>
+__device__ __forceinline__ void dft_small(double2 (&a)[R])
 {
-    int h = 1;
-    if (ilog2(M) & 1) {
-        __syncthreads();
-        for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
-            const double2 u = x[2 * b], v = x[2 * b + 1];
-            x[2 * b] = cadd(u, v);
-            x[2 * b + 1] = csub(u, v);
+    if constexpr (R == 2) {
+        const double2 u = a[0];
+        a[0] = cadd(u, a[1]);
+        a[1] = csub(u, a[1]);
+    } else if constexpr (R == 4) {
+        const double2 s0 = cadd(a[0], a[2]), s1 = csub(a[0], a[2]);
+        const double2 s2 = cadd(a[1], a[3]), d = csub(a[1], a[3]);
+        const double2 s3 = S > 0 ? times_i(d) : make_double2(d.y, -d.x);   // S i (a1 - a3)
+        a[0] = cadd(s0, s2);
+        a[1] = cadd(s1, s3);
+        a[2] = csub(s0, s2);
+        a[3] = csub(s1, s3);
+    } else {
+        // odd R: pair p with R - p, y_q = A_q + S i B_q, y_{R-q} = A_q - S i B_q
+        constexpr int H = (R - 1) / 2, O = root_off<R>();
+        double2 sp[H], dp[H];
+#pragma unroll
+        for (int p = 1; p <= H; ++p) {
+            sp[p - 1] = cadd(a[p], a[R - p]);
+            dp[p - 1] = csub(a[p], a[R - p]);
         }
-        h = 2;
+        const double2 a0 = a[0];
+        double2 y0 = a0;
+#pragma unroll
+        for (int p = 0; p < H; ++p) y0 = cadd(y0, sp[p]);
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            double2 A = a0, B = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int p = 1; p <= H; ++p) {
+                const double c = kRootCos[O + (p * q) % R], sn = kRootSin[O + (p * q) % R];
+                A.x = fma(sp[p - 1].x, c, A.x);
+                A.y = fma(sp[p - 1].y, c, A.y);
+                B.x = fma(dp[p - 1].x, sn, B.x);
+                B.y = fma(dp[p - 1].y, sn, B.y);
+            }
+            const double2 iB = S > 0 ? make_double2(-B.y, B.x) : make_double2(B.y, -B.x);
+            a[q] = cadd(A, iB);
+            a[R - q] = csub(A, iB);
+        }
+        a[0] = y0;
     }
-    for (; h < M; h *= 4) {
-        __syncthreads();
-        const int S = Wlen / (4 * h);
-        for (int b = threadIdx.x; b < M / 4; b += blockDim.x) {
-            const int j = b % h;
-            const int base = (b - j) * 4 + j;
-            const double2 a = x[base];
-            const double2 t1 = cmul(__ldg(W + (size_t)2 * j * S), x[base + h]);
-            const double2 t2 = cmul(__ldg(W + (size_t)j * S), x[base + 2 * h]);
-            const double2 t3 = cmul(__ldg(W + (size_t)3 * j * S), x[base + 3 * h]);
-            const double2 p = cadd(a, t1), m = csub(a, t1);
-            const double2 sp = cadd(t2, t3), sm = times_i(csub(t2, t3));
-            x[base] = cadd(p, sp);
-            x[base + h] = cadd(m, sm);
-            x[base + 2 * h] = csub(p, sp);
-            x[base + 3 * h] = csub(m, sm);
+}
+
+// one pass of radix R over N points in blocks of B; tw(t) = e^{2 pi i t / N}
+template <int R, bool INV, class TW>
+__device__ __forceinline__ void mx_pass(double2 *x, int N, int B, const TW &tw)
+{
+    const int Ns = B / R, step = N / B;
+    for (int t = threadIdx.x; t < N / R; t += blockDim.x) {
+        const int j = t % Ns, base = (t - j) * R + j;
+        double2 a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = x[base + q * Ns];
+        if (INV) {
+            if (j) {
+#pragma unroll
+                for (int p = 1; p < R; ++p) a[p] = cmul(a[p], tw(p * j * step));
+            }
+            dft_small<R, 1>(a);
+        } else {
+            dft_small<R, -1>(a);
+            if (j) {
+#pragma unroll
+                for (int p = 1; p < R; ++p) a[p] = cmul_conj(a[p], tw(p * j * step));
+            }
         }
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[base + q * Ns] = a[q];
+    }
+}
+
+// BIG: the radix-11 and radix-13 butterflies are compiled in (they need many
+// more registers; only lengths with those factors are run with BIG)
+template <bool INV, bool BIG, class TW>
+__device__ __forceinline__ void mx_pass_any(int r, double2 *x, int N, int B, const TW &tw)
+{
+    switch (r) {
+    case 4: mx_pass<4, INV>(x, N, B, tw); break;
+    case 2: mx_pass<2, INV>(x, N, B, tw); break;
+    case 3: mx_pass<3, INV>(x, N, B, tw); break;
+    case 5: mx_pass<5, INV>(x, N, B, tw); break;
+    case 7: mx_pass<7, INV>(x, N, B, tw); break;
+    default:
+        if constexpr (BIG) {
+            if (r == 11) mx_pass<11, INV>(x, N, B, tw);
+            else mx_pass<13, INV>(x, N, B, tw);
+        }
+        break;
+    }
+}
+
+// natural order in, position order out, exponent -1
+template <bool BIG, class TW>
+__device__ void fft_mx_dif(double2 *x, int N, const int *__restrict__ rl, const TW &tw)
+{
+    const int n = rl[0];
+    int B = N;
+    for (int i = 0; i < n; ++i) {
+        const int r = rl[1 + i];
+        __syncthreads();
+        mx_pass_any<false, BIG>(r, x, N, B, tw);
+        B /= r;
     }
     __syncthreads();
 }
 
-// Decimation in frequency, negative exponent: natural in, bit-reversed out.
-// Radix-4 passes fusing the stages of half-size H and H/2 (w = conj of the
-// 2H-th root): with s0 = a+c, s1 = a-c, s2 = b+d, s3 = b-d,
-//   a' = s0+s2,  b' = (s0-s2) w^{2j},  c' = (s1 - i s3) w^{j},  d' = (s1 + i s3) w^{3j};
-// an odd number of stages ends with one twiddle-free radix-2 pass.
-static __device__ void fft_dif_forward(double2 *x, int M, const double2 *__restrict__ W, int Wlen)
+// position order in, natural order out, exponent +1 (unnormalised)
+template <bool BIG, class TW>
+__device__ void fft_mx_dit(double2 *x, int N, const int *__restrict__ rl, const TW &tw)
 {
-    int H = M / 2;
-    for (; H >= 2; H /= 4) {
+    const int n = rl[0];
+    int B = 1;
+    for (int i = n - 1; i >= 0; --i) {
+        const int r = rl[1 + i];
+        B *= r;
         __syncthreads();
-        const int S = Wlen / (2 * H), Q = H / 2;
-        for (int b = threadIdx.x; b < M / 4; b += blockDim.x) {
-            const int j = b % Q;
-            const int base = (b - j) * 4 + j;
-            const double2 a = x[base], bb = x[base + Q], c = x[base + H], d = x[base + H + Q];
-            const double2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(bb, d), s3 = csub(bb, d);
-            x[base] = cadd(s0, s2);
-            x[base + Q] = cmul_conj(csub(s0, s2), __ldg(W + (size_t)2 * j * S));
-            x[base + H] = cmul_conj(cadd(s1, times_mi(s3)), __ldg(W + (size_t)j * S));
-            x[base + H + Q] = cmul_conj(cadd(s1, times_i(s3)), __ldg(W + (size_t)3 * j * S));
-        }
-    }
-    if (H == 1) {
-        __syncthreads();
-        for (int b = threadIdx.x; b < M / 2; b += blockDim.x) {
-            const double2 u = x[2 * b], v = x[2 * b + 1];
-            x[2 * b] = cadd(u, v);
-            x[2 * b + 1] = csub(u, v);
-        }
+        mx_pass_any<true, BIG>(r, x, N, B, tw);
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ int bitrev(int k, int logn)
+// ring transform kinds: direct mixed radix over 2, 3, 4, 5, 7; Bluestein
+// (7-smooth convolution length); direct with radix 11 or 13 among the radices
+enum RingFft { kDirect = 0, kBluestein = 1, kDirectBig = 2 };
+
+// position of X_k in position order
+__device__ __forceinline__ int fft_pos(int k, int N, const int *__restrict__ rl)
 {
-    return logn == 0 ? 0 : (int)(__brev((unsigned)k) >> (32 - logn));
+    const int n = rl[0];
+    int pos = 0, Nc = N;
+    for (int i = 0; i < n; ++i) {
+        const int r = rl[1 + i];
+        Nc /= r;
+        pos += (k % r) * Nc;
+        k /= r;
+    }
+    return pos;
 }
+
+// e^{2 pi i t / K} (t < K) from the ring's half-circle table of J = 2K roots
+struct TwRing {
+    const double2 *T;
+    int J;
+    __device__ __forceinline__ double2 operator()(int t) const
+    {
+        const int n = 4 * t;             // e^{2 pi i t / K} = e^{i pi 4t / J}, 4t < 2J
+        if (n < J) return __ldg(T + n);
+        const double2 u = __ldg(T + (n - J));
+        return make_double2(-u.x, -u.y);
+    }
+};
+
+// e^{2 pi i t / M} (t < M) from a table of M roots
+struct TwTable {
+    const double2 *R;
+    __device__ __forceinline__ double2 operator()(int t) const { return __ldg(R + t); }
+};
 
 // x[0..K) holds the input; computes x[n] = sum_k x_k e^{2 pi i k n / K} in
-// place for n < K (x must hold M entries).  T is the ring's e^{i pi n/J}
-// table with J = 2K, so the chirp c_j = e^{i pi j^2 / K} = T-root(2 j^2).
-static __device__ void bluestein_inverse(double2 *x, int K, int M, const double2 *__restrict__ T,
-                                  const double2 *__restrict__ fb, const double2 *__restrict__ W,
-                                  int Wlen)
+// place for n < K through Bluestein's chirp transform: a cyclic convolution
+// of length M (smooth, >= 2K - 1) with the chirp filter, stored transformed
+// in position order and scaled by 1/M.  x must hold M entries.  T is the
+// ring's e^{i pi n/J} table (J = 2K): the chirp c_j = e^{i pi j^2 / K} is
+// the root of index 2 j^2 mod 2J.
+static __device__ void bluestein_mx(double2 *x, int K, int M, const double2 *__restrict__ T,
+                             const double2 *__restrict__ fb, const int *__restrict__ rl, const TwTable &tw)
 {
     const int J = 2 * K;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         if (k < K) x[k] = cmul(x[k], ring_root(T, J, 2LL * k * k));
         else x[k] = make_double2(0.0, 0.0);
     }
-    fft_dif_forward(x, M, W, Wlen);
+    fft_mx_dif<false>(x, M, rl, tw);
     for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = cmul(x[k], __ldg(fb + k));
-    fft_dit_inverse(x, M, W, Wlen);
+    fft_mx_dit<false>(x, M, rl, tw);
     for (int n = threadIdx.x; n < K; n += blockDim.x) x[n] = cmul(x[n], ring_root(T, J, 2LL * n * n));
     __syncthreads();
 }
@@ -166,14 +296,14 @@ static __device__ void bluestein_inverse(double2 *x, int K, int M, const double2
 // Hermitian spectrum into a half-length complex FFT, transform, and write
 // f_{2n}, f_{2n+1} as the real and imaginary parts of z_n.  All threads of
 // the block take part; sm holds K (power of two) or M (Bluestein) entries.
-template <bool BLUE, class QAt>
+template <int KIND, class QAt>
 __device__ void phi_synth_ring_at(const PlanView &v, int ring, QAt qat, double *out_ring, double2 *sm)
 {
+    constexpr bool BLUE = KIND == kBluestein;
     const int L = v.lmax;
     const int J = v.ring_J[ring], K = J / 2, s = v.ring_s[ring];
     const double2 *__restrict__ T = v.tw + v.ring_tw[ring];
-    int logK = 0;
-    while ((1 << logK) < K) ++logK;
+    const int *__restrict__ rl = v.rad + v.ring_rad[ring];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const double2 g0 = fold_G(qat, L, J, s, k);
         double2 g1 = fold_G(qat, L, J, s, k + K);
@@ -182,13 +312,13 @@ __device__ void phi_synth_ring_at(const PlanView &v, int ring, QAt qat, double *
         double2 Zk = cadd(E, times_i(cmul(ring_root(T, J, 2LL * k), O)));
         if (s) Zk = cmul(Zk, ring_root(T, J, k));          // common factor e^{i pi k s / J}
         if (BLUE) sm[k] = Zk;
-        else sm[bitrev(k, logK)] = Zk;
+        else sm[fft_pos(k, K, rl)] = Zk;
     }
-    if (BLUE) {
+    if constexpr (BLUE) {
         __syncthreads();
-        bluestein_inverse(sm, K, v.ring_M[ring], T, v.fb + v.ring_fb[ring], v.W, v.Wlen);
+        bluestein_mx(sm, K, v.ring_mx[ring], T, v.mfb + v.ring_mfb[ring], rl, TwTable{v.mtw + v.ring_mtw[ring]});
     } else {
-        fft_dit_inverse(sm, K, v.W, v.Wlen);
+        fft_mx_dit<KIND == kDirectBig>(sm, K, rl, TwRing{T, J});
     }
     double2 *out = reinterpret_cast<double2 *>(out_ring);
     for (int n = threadIdx.x; n < K; n += blockDim.x) out[n] = sm[n];
@@ -196,17 +326,17 @@ __device__ void phi_synth_ring_at(const PlanView &v, int ring, QAt qat, double *
 }
 
 // ... with q_m read from a ring-major array qr[m]
-template <bool BLUE, bool CG>
+template <int KIND, bool CG>
 __device__ void phi_synth_ring(const PlanView &v, int ring, const double2 *qr, double *out_ring,
                                double2 *sm)
 {
-    phi_synth_ring_at<BLUE>(v, ring, [qr](int m) { return ldq<CG>(qr + m); }, out_ring, sm);
+    phi_synth_ring_at<KIND>(v, ring, [qr](int m) { return ldq<CG>(qr + m); }, out_ring, sm);
 }
 
 // ... with q_m formed from the two parity halves of the butterfly output,
 // stored map-major: qt[((b * 2 + t) * nhalf + r) * (L + 1) + m] (complex);
 // north rings (ring < nhalf) take q^0 + q^1, their mirrors q^0 - q^1.
-template <bool BLUE, bool CG>
+template <int KIND, bool CG>
 __device__ void phi_synth_ring_qt(const PlanView &v, int ring, const double2 *qt, int b,
                                   double *out_ring, double2 *sm)
 {
@@ -221,7 +351,7 @@ __device__ void phi_synth_ring_qt(const PlanView &v, int ring, const double2 *qt
         const double2 x1 = ldq<CG>(q1 + m);
         return north ? make_double2(x0.x + x1.x, x0.y + x1.y) : make_double2(x0.x - x1.x, x0.y - x1.y);
     };
-    phi_synth_ring_at<BLUE>(v, ring, qat, out_ring, sm);
+    phi_synth_ring_at<KIND>(v, ring, qat, out_ring, sm);
 }
 
 }  // namespace shtb_dev

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
 #include <thread>
 #include <vector>
 
@@ -196,6 +197,64 @@ void dif_forward(std::vector<std::complex<double>> &x, const std::vector<std::co
                 x[blk + j + half] = (u - v) * w;
             }
         }
+    }
+}
+
+// Radices of a mixed-radix transform of length n over 4, 2, 3, 5, 7, 11, 13
+// (4s first, at most one 2); false if n has another prime factor.
+bool radix_list(long long n, std::vector<int> &rl)
+{
+    rl.clear();
+    if (n < 1) return false;
+    int twos = 0;
+    while (n % 2 == 0) { n /= 2; ++twos; }
+    for (; twos >= 2; twos -= 2) rl.push_back(4);
+    if (twos) rl.push_back(2);
+    for (int pr : {3, 5, 7, 11, 13})
+        while (n % pr == 0) { n /= pr; rl.push_back(pr); }
+    return n == 1;
+}
+
+// smallest 7-smooth integer >= n
+long long smooth_at_least(long long n)
+{
+    for (long long m = std::max(1LL, n);; ++m) {
+        long long x = m;
+        for (int pr : {2, 3, 5, 7})
+            while (x % pr == 0) x /= pr;
+        if (x == 1) return m;
+    }
+}
+
+// In-place mixed-radix decimation in frequency with exponent -1 (the device
+// kernels' pass structure): natural-order input, position-order output.
+void mixed_dif_forward(std::vector<std::complex<double>> &x, const std::vector<int> &rl)
+{
+    const long long N = (long long)x.size();
+    std::vector<std::complex<double>> w(N);          // e^{-2 pi i t / N}
+    for (long long t = 0; t < N; ++t) {
+        double c, sn;
+        sincospi_frac(2 * t, N, &c, &sn);
+        w[t] = {c, -sn};
+    }
+    long long B = N;
+    std::vector<std::complex<double>> a, y;
+    for (int r : rl) {
+        const long long Ns = B / r, step = N / B, rs = N / r;
+        a.resize(r);
+        y.resize(r);
+        for (long long b = 0; b < N; b += B) {
+            for (long long j = 0; j < Ns; ++j) {
+                for (int q = 0; q < r; ++q) a[q] = x[b + j + q * Ns];
+                for (int p = 0; p < r; ++p) {
+                    std::complex<double> acc = 0.0;
+                    for (int q = 0; q < r; ++q) acc += a[q] * w[((p * q) % r) * rs];
+                    y[p] = acc * w[p * j * step];
+                }
+                for (int p = 0; p < r; ++p) x[b + j + p * Ns] = y[p];
+            }
+        }
+        B = Ns;
     }
 }
 
@@ -438,25 +497,24 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     p->stats.legendre_flops_per_map = 4.0 * (double)n_rec;
 
     // ------------------------------------------------------- ring FFT tables
-    // Per ring: K = J/2 (J is always even); K a power of two -> in-place
-    // radix-2 FFT, otherwise Bluestein with M = next_pow2(2K - 1).
+    // Per ring: K = J/2 (J is always even).  Radix-2 tables for the batch
+    // kernel: K a power of two -> in-place radix-2 FFT, otherwise Bluestein
+    // with M = next_pow2(2K - 1).
     p->ring_M.assign(p->nrings, 0);
     std::vector<long long> ring_tw(p->nrings), ring_fb(p->nrings, -1);
-    p->pow2_rings.clear();
-    p->blue_rings.clear();
+    std::vector<int> pow2_blue;
     p->max_K_pow2 = 0;
     p->max_M_blue = 0;
     long long Wlen = 2;
     for (int r = 0; r < p->nrings; ++r) {
         long long K = p->ring_J[r] / 2;
         if (is_pow2(K)) {
-            p->pow2_rings.push_back(r);
             p->max_K_pow2 = std::max<long long>(p->max_K_pow2, K);
             Wlen = std::max(Wlen, K);
         } else {
             long long M = next_pow2(2 * K - 1);
             p->ring_M[r] = (int)M;
-            p->blue_rings.push_back(r);
+            pow2_blue.push_back(r);
             p->max_M_blue = std::max<long long>(p->max_M_blue, M);
             Wlen = std::max(Wlen, M);
         }
@@ -494,7 +552,7 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     // stored as DIF_forward(b) / M in bit-reversed order.
     std::vector<long long> fb_of_J(4 * N + 1, -1);
     std::vector<int> distinct;
-    for (int r : p->blue_rings)
+    for (int r : pow2_blue)
         if (fb_of_J[p->ring_J[r]] < 0) { fb_of_J[p->ring_J[r]] = 0; distinct.push_back(p->ring_J[r]); }
     std::vector<long long> fb_off(distinct.size());
     long long fb_total = 0;
@@ -518,7 +576,103 @@ int shtb_build_dense_plan(shtb_plan_s *p)
         for (long long k = 0; k < M; ++k)
             fb[fb_off[d] + k] = make_double2(bv[k].real() / M, bv[k].imag() / M);
     });
-    for (int r : p->blue_rings) ring_fb[r] = fb_of_J[p->ring_J[r]];
+    for (int r : pow2_blue) ring_fb[r] = fb_of_J[p->ring_J[r]];
+
+    // Mixed-radix tables of the stand-alone ring kernels: K factoring over
+    // 2, 3, 5, 7, 11, 13 -> direct transform of length K; otherwise Bluestein
+    // through the smallest 7-smooth length M >= 2K - 1.
+    std::vector<int> rad, ring_rad(p->nrings), ring_mx(p->nrings, 0);
+    std::vector<long long> ring_mfb(p->nrings, 0), ring_mtw(p->nrings, 0);
+    std::vector<double2> mfb, mtw;
+    {
+        std::map<long long, int> rad_of_len;
+        std::map<long long, long long> mtw_of_len;
+        std::vector<long long> mfb_of_J(4 * N + 1, -1);
+        auto radix_off = [&](long long n) {
+            auto it = rad_of_len.find(n);
+            if (it != rad_of_len.end()) return it->second;
+            std::vector<int> rl;
+            radix_list(n, rl);
+            const int off = (int)rad.size();
+            rad.push_back((int)rl.size());
+            rad.insert(rad.end(), rl.begin(), rl.end());
+            rad_of_len[n] = off;
+            return off;
+        };
+        std::vector<int> blue_J;
+        p->direct_rings.clear();
+        p->blue_rings.clear();
+        p->big_rings.clear();
+        p->max_K_direct = 0;
+        p->max_M_mx = 0;
+        p->max_K_big = 0;
+        for (int r = 0; r < p->nrings; ++r) {
+            const long long K = p->ring_J[r] / 2;
+            std::vector<int> rl;
+            if (radix_list(K, rl)) {
+                ring_rad[r] = radix_off(K);
+                const bool big = std::any_of(rl.begin(), rl.end(), [](int x) { return x > 7; });
+                (big ? p->big_rings : p->direct_rings).push_back(r);
+                int &mx = big ? p->max_K_big : p->max_K_direct;
+                mx = std::max<int>(mx, (int)K);
+            } else {
+                const long long M = smooth_at_least(2 * K - 1);
+                ring_mx[r] = (int)M;
+                ring_rad[r] = radix_off(M);
+                p->blue_rings.push_back(r);
+                p->max_M_mx = std::max<long long>(p->max_M_mx, M);
+                if (!mtw_of_len.count(M)) {
+                    mtw_of_len[M] = (long long)mtw.size();
+                    for (long long t = 0; t < M; ++t) {
+                        double c, sn;
+                        sincospi_frac(2 * t, M, &c, &sn);
+                        mtw.push_back(make_double2(c, sn));
+                    }
+                }
+                ring_mtw[r] = mtw_of_len[M];
+                if (mfb_of_J[p->ring_J[r]] < 0) {
+                    mfb_of_J[p->ring_J[r]] = 0;
+                    blue_J.push_back(p->ring_J[r]);
+                }
+            }
+        }
+        if ((long long)std::max({p->max_K_direct, p->max_M_mx, p->max_K_big}) * 16 > 200 * 1024)
+            return shtb_fail(SHTB_ENOTSUP, "ring FFT does not fit in shared memory (nside too large)");
+        // Bluestein filters, one per distinct J: the DIF transform of
+        // b_j = conj(c_j) (|j| < K, cyclic in M) in position order, / M
+        std::vector<long long> off(blue_J.size());
+        long long total = 0;
+        for (size_t d = 0; d < blue_J.size(); ++d) {
+            off[d] = total;
+            mfb_of_J[blue_J[d]] = total;
+            total += smooth_at_least(2 * (blue_J[d] / 2) - 1);
+        }
+        mfb.resize((size_t)total);
+        parallel_for((int)blue_J.size(), nthreads, [&](int d) {
+            const long long K = blue_J[d] / 2, M = smooth_at_least(2 * K - 1);
+            std::vector<std::complex<double>> bv(M, 0.0);
+            for (long long j = 0; j < K; ++j) {
+                double c, sn;
+                sincospi_frac((j * j) % (2 * K), K, &c, &sn);
+                std::complex<double> b(c, -sn);
+                bv[j] = b;
+                if (j > 0) bv[M - j] = b;
+            }
+            std::vector<int> rl;
+            radix_list(M, rl);
+            mixed_dif_forward(bv, rl);
+            for (long long k = 0; k < M; ++k)
+                mfb[off[d] + k] = make_double2(bv[k].real() / M, bv[k].imag() / M);
+        });
+        for (int r : p->blue_rings) ring_mfb[r] = mfb_of_J[p->ring_J[r]];
+        // heaviest rings first
+        std::stable_sort(p->direct_rings.begin(), p->direct_rings.end(),
+                         [&](int a, int b) { return p->ring_J[a] > p->ring_J[b]; });
+        std::stable_sort(p->big_rings.begin(), p->big_rings.end(),
+                         [&](int a, int b) { return p->ring_J[a] > p->ring_J[b]; });
+        std::stable_sort(p->blue_rings.begin(), p->blue_rings.end(),
+                         [&](int a, int b) { return ring_mx[a] > ring_mx[b]; });
+    }
 
     // algorithmic FFT flops: 2.5 J log2 J per real ring transform of length J
     double phi_flops = 0.0;
@@ -553,18 +707,28 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     UP(ring_start, p->ring_start);
     UP(ring_tw, ring_tw);
     UP(tw, tw);
+    UP(ring_rad, ring_rad);
+    UP(rad, rad);
+    UP(ring_mx, ring_mx);
+    UP(ring_mfb, ring_mfb);
+    UP(mfb, mfb);
+    UP(ring_mtw, ring_mtw);
+    UP(mtw, mtw);
     UP(ring_M, p->ring_M);
     UP(ring_fb, ring_fb);
     UP(fb, fb);
     UP(W, W);
 #undef UP
     void *d;
-    rc = plan_alloc_upload(p, &d, p->pow2_rings.data(), sizeof(int) * p->pow2_rings.size());
+    rc = plan_alloc_upload(p, &d, p->direct_rings.data(), sizeof(int) * p->direct_rings.size());
     if (rc) return rc;
-    p->d_pow2_rings = (int *)d;
+    p->d_direct_rings = (int *)d;
     rc = plan_alloc_upload(p, &d, p->blue_rings.data(), sizeof(int) * p->blue_rings.size());
     if (rc) return rc;
     p->d_blue_rings = (int *)d;
+    rc = plan_alloc_upload(p, &d, p->big_rings.data(), sizeof(int) * p->big_rings.size());
+    if (rc) return rc;
+    p->d_big_rings = (int *)d;
 
     // bytes one call reads from the plan (Legendre tables + start values)
     p->stats.plan_read_bytes = (long long)(sizeof(RecCoef) * coef.size() + sizeof(int) * jstart.size() +

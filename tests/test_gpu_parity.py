@@ -209,6 +209,42 @@ def test_compressed_synthesis_vs_oracle(nside, lmax, eps):
     plan.close()
 
 
+@pytest.mark.parametrize("nside,lmax,eps", [(32, 64, 1e-12), (64, 100, 1e-10), (13, 30, 1e-8)])
+def test_compressed_legendre_stage_parity_halves(nside, lmax, eps):
+    """shtb_test_butterfly: residual blocks and butterfly levels alone give
+    the parity halves q^0, q^1 on the half-rings (Eq. q-even-odd2); against
+    the oracle's q_m(z) on a ring and its mirror, (q(z) + q(-z))/2 and
+    (q(z) - q(-z))/2, within the compression tolerance."""
+    plan = sh.Plan(nside, lmax, eps)
+    Z = 2 * nside
+    rings = oracle.healpix_rings(nside)
+    a = synthetic.gaussian_alm(lmax, 2, seed=91)
+    q = oracle.legendre_q(rings, lmax, a)                     # [b, nrings, L+1]
+    nr = 4 * nside - 1
+    north = q[:, :Z, :]
+    south = q[:, [nr - 1 - r if r < Z - 1 else r for r in range(Z)], :]   # mirror (equator itself)
+    want = np.stack([(north + south) / 2, (north - south) / 2], axis=1)    # [b, 2, Z, L+1]
+    want[:, 1, Z - 1, :] = 0.0                                # odd parity vanishes on the equator
+    qt = torch.empty((2, 2, Z, lmax + 1), dtype=torch.complex128, device="cuda")
+    sh.shtb_test_butterfly(plan.handle, dev(a), qt, 2)
+    got = qt.cpu().numpy()
+    tol = 1e-10 if eps <= 1e-12 else 100 * eps
+    scale = np.sqrt(np.mean(np.abs(want) ** 2))
+    assert np.sqrt(np.mean(np.abs(got - want) ** 2)) <= tol * scale
+    assert np.all(got[:, 1, :, lmax] == 0)                     # chain (m = L, t = 1) is empty
+    plan.close()
+
+
+def test_butterfly_stage_needs_compressed_plan():
+    plan = sh.Plan(8, 16, 0.0)
+    a = torch.zeros((1, plan.nalm), dtype=torch.complex128, device="cuda")
+    qt = torch.empty((1, 2, 16, 17), dtype=torch.complex128, device="cuda")
+    with pytest.raises(sh.ShtbError) as e:
+        sh.shtb_test_butterfly(plan.handle, a, qt, 1)
+    assert e.value.code == sh.SHTB_ENOTSUP
+    plan.close()
+
+
 def test_compressed_batches_match_single_maps():
     plan = sh.Plan(64, 128, 1e-10)
     a = dev(synthetic.gaussian_alm(128, 11, seed=3))
