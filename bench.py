@@ -335,12 +335,119 @@ def run_ours(args, rank, world, dist):
                     "depth_hist": st["depth_hist"][:12],
                     "legendre_flops_per_step": flops_leg},
     }
+    plan.close()
+    del alm, maps, f, aout
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_patterns:
+        out["details"]["batched_serving"], plan_c4 = batched_serving(sh, synthetic, dev)
+        out["details"]["differentiation"] = differentiation(sh, synthetic, dev, plan_c4)
+        plan_c4.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, cores, sample = oracle_sample(N, L, 1, args.cpu_rings, seed=2000)
         out["cpu_baseline"] = {"value": round(ms_cpu, 1), "unit": UNIT, "cores": cores,
                                "kind": "oracle", "sample": sample}
-    plan.close()
     return out
+
+
+def event_ms(fn, reps):
+    """Mean CUDA-event time of fn on the current stream (one warm-up call)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_serving(sh, synthetic, dev, reps=5):
+    """Pattern 2 on the uneven request mix: 64 requests, Nside drawn from
+    {64, ..., 1024} and 1-8 maps each (numpy default_rng(3000)), L = 2 Nside,
+    eps = 1e-10; one persistent launch (graph replay) against the plain
+    one-request-per-launch loop on the same plans.  Returns the summary and
+    the Nside=1024 plan (reused for the differentiation workload)."""
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(3000)
+    sizes = (64, 128, 256, 512, 1024)
+    t0 = time.perf_counter()
+    plans = {n: sh.Plan(n, 2 * n, 1e-10) for n in sizes}
+    build_s = time.perf_counter() - t0
+    reqs = []
+    for i in range(64):
+        n = int(rng.choice(sizes))
+        b = int(rng.integers(1, 9))
+        alm = torch.from_numpy(synthetic.gaussian_alm(2 * n, b, seed=3000 + 10 * i)).to(dev)
+        reqs.append((plans[n], alm, torch.empty((b, plans[n].npix), dtype=torch.float64, device=dev)))
+    nmaps = sum(int(r[1].shape[0]) for r in reqs)
+    t0 = time.perf_counter()
+    batch = sh.shtb_batch_create(reqs, autotune=True)
+    create_s = time.perf_counter() - t0
+    info = sh.shtb_batch_info(batch)
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for p, alm, maps in reqs:
+            p.synthesize(alm, out=maps)
+
+    ms_plain = event_ms(plain, reps)
+    want = [m.clone() for _, _, m in reqs]
+    ms_batch = event_ms(lambda: sh.shtb_batch_run(batch, stream), reps)
+    sh.shtb_batch_status(batch, stream)
+    diff = max(float((m - w).abs().max() / w.abs().max()) for (_, _, m), w in zip(reqs, want))
+    sh.shtb_batch_destroy(batch)
+    for n in sizes[:-1]:
+        plans[n].close()
+    return ({"requests": 64, "maps": nmaps, "plans": len(sizes), "eps": 1e-10,
+             "batched_ms": round(ms_batch, 3), "plain_ms": round(ms_plain, 3),
+             "batched_over_plain": round(ms_plain / ms_batch, 3),
+             "maps_per_s_batched": round(nmaps / (ms_batch * 1e-3), 1),
+             "max_rel_diff_vs_plain": diff, "schedule": info,
+             "plan_build_s": round(build_s, 1), "create_and_tune_s": round(create_s, 1)},
+            plans[sizes[-1]])
+
+
+def differentiation(sh, synthetic, dev, plan, reps=5):
+    """Pattern 3: loss = 0.5 ||Y a - d||^2 at Nside=1024, L=2048, 4 maps,
+    d = Y a_true + 0.1 N(0, 1) per pixel; forward + backward through the
+    autograd Function (backward = the adjoint kernels), and a directional
+    derivative check (exact for a quadratic loss up to rounding)."""
+    import numpy as np
+    import torch
+
+    B, L = 4, plan.lmax
+    a_true = torch.from_numpy(np.stack([synthetic.gaussian_alm(L, 1, seed=4100 + b)[0] for b in range(B)])).to(dev)
+    a0 = torch.from_numpy(np.stack([synthetic.gaussian_alm(L, 1, seed=4000 + b)[0] for b in range(B)])).to(dev)
+    noise = torch.from_numpy(np.random.default_rng(4200).normal(0.0, 0.1, (B, plan.npix))).to(dev)
+    with torch.no_grad():
+        d = plan.synthesize(a_true) + noise
+
+    def loss_of(a):
+        r = sh.synthesize(a, plan) - d
+        return 0.5 * (r * r).sum()
+
+    a = a0.clone().requires_grad_(True)
+
+    def step():
+        a.grad = None
+        loss_of(a).backward()
+
+    ms = event_ms(step, reps)
+    g = a.grad.detach().clone()
+    v = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=4300)).to(dev)
+    v[:, :L + 1] = v[:, :L + 1].real.to(v.dtype)     # Im a_l0 is ignored by the transform
+    h = 1e-3
+    with torch.no_grad():
+        fd = (loss_of(a0 + h * v) - loss_of(a0 - h * v)) / (2 * h)
+    dd = float((g.conj() * v).real.sum())
+    return {"nside": plan.nside, "lmax": L, "maps": B, "eps": plan.eps,
+            "fwd_bwd_ms": round(ms, 3), "fwd_bwd_ms_per_map": round(ms / B, 3),
+            "directional_derivative_rel_err": abs(float(fd) - dd) / abs(dd)}
 
 
 def run_reference(args):
@@ -382,6 +489,8 @@ def main():
     ap.add_argument("--cpu-rings", type=int, default=64, help="ring sample of the CPU baseline")
     ap.add_argument("--ref-rings", type=int, default=16, help="ring sample per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the batched-serving and differentiation measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
