@@ -196,6 +196,9 @@ typedef struct {
     int group_width;         /* maps per operator read, 1..8 (default 8)               */
     int lpt;                 /* 1: largest items first inside each stage               */
     long long spin_limit;    /* polls before a stage wait gives up (0 = 2e7)           */
+    int schedule;            /* without autotune: 0 = one persistent kernel launch,
+                                1 = graph of the stage kernels over merged map groups  */
+    int streams;             /* streams of schedule 1 (0 = 4)                           */
 } shtb_batch_opts;
 
 int shtb_batch_opts_init(shtb_batch_opts *opts);
@@ -222,11 +225,15 @@ int shtb_batch_run(shtb_batch batch, void *stream);
 int shtb_batch_status(shtb_batch batch, void *stream);
 
 /* Schedule chosen for the batch: warps per block, persistent grid size,
-   number of work packs and the autotuner's best time (ms, 0 if not tuned). */
+   number of work packs (all 0 for the stage-kernel schedule) and the
+   autotuner's best time (ms, 0 if not tuned). */
 int shtb_batch_info(shtb_batch batch, int *warps_per_block, int *grid, int *npacks,
                     double *tuned_ms);
 
 int shtb_batch_destroy(shtb_batch batch);
+/* The schedule in use: 0 = persistent kernel, 1 = stage-kernel graph, and
+   the stream count of schedule 1 (0 for schedule 0). */
+int shtb_batch_schedule(shtb_batch batch, int *schedule, int *streams);
 
 /* Private test hook: with on = 1 the batch's first stage claims one item more
    than it has, so every later stage's bounded wait runs out and the next run

@@ -71,7 +71,8 @@ class Request(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("group_width", ctypes.c_int), ("lpt", ctypes.c_int),
-                ("spin_limit", ctypes.c_longlong)]
+                ("spin_limit", ctypes.c_longlong), ("schedule", ctypes.c_int),
+                ("streams", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -109,6 +110,7 @@ SIGNATURES = {
     "shtb_batch_status": (_I, [_P, _P]),
     "shtb_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
     "shtb_batch_destroy": (_I, [_P]),
+    "shtb_batch_schedule": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "shtb_test_batch_stall": (_I, [_P, _I]),
     "shtb_test_host_id": (_I, [_I, _I, _DP, _D, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
     "shtb_test_host_butterfly": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
@@ -349,7 +351,8 @@ def shtb_batch_opts_init() -> BatchOpts:
 
 
 def shtb_batch_create(requests, autotune: bool = True, warps_per_block: int = 0,
-                      group_width: int = 8, lpt: bool = True, spin_limit: int = 0):
+                      group_width: int = 8, lpt: bool = True, spin_limit: int = 0,
+                      schedule: int = 0, streams: int = 0):
     """requests: iterable of (plan, alm tensor [nmaps, nalm] complex128, maps tensor
     [nmaps, npix] float64), all on the current CUDA device."""
     import torch
@@ -365,6 +368,7 @@ def shtb_batch_create(requests, autotune: bool = True, warps_per_block: int = 0,
     o = shtb_batch_opts_init()
     o.autotune, o.warps_per_block, o.group_width = int(autotune), warps_per_block, group_width
     o.lpt, o.spin_limit = int(lpt), spin_limit
+    o.schedule, o.streams = schedule, streams
     h = ctypes.c_void_p()
     _check(lib().shtb_batch_create(arr, len(reqs), ctypes.byref(o), ctypes.byref(h)),
            "shtb_batch_create")
@@ -383,7 +387,15 @@ def shtb_batch_info(batch) -> dict:
     w, g, n, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().shtb_batch_info(batch, ctypes.byref(w), ctypes.byref(g), ctypes.byref(n),
                                  ctypes.byref(t)), "shtb_batch_info")
-    return {"warps_per_block": w.value, "grid": g.value, "npacks": n.value, "tuned_ms": t.value}
+    out = {"warps_per_block": w.value, "grid": g.value, "npacks": n.value, "tuned_ms": t.value}
+    out.update(shtb_batch_schedule(batch))
+    return out
+
+
+def shtb_batch_schedule(batch) -> dict:
+    s, n = ctypes.c_int(), ctypes.c_int()
+    _check(lib().shtb_batch_schedule(batch, ctypes.byref(s), ctypes.byref(n)), "shtb_batch_schedule")
+    return {"schedule": s.value, "streams": n.value}
 
 
 def shtb_batch_destroy(batch) -> None:

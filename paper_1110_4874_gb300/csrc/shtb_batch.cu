@@ -1,5 +1,7 @@
 // Batched serving: many synthesis requests of different (Nside, L, eps) in
-// ONE persistent kernel launch, captured in a CUDA graph on the first run.
+// ONE persistent kernel launch, captured in a CUDA graph on the first run --
+// or, where the autotuner finds it faster, a CUDA graph of the stand-alone
+// stage kernels over the merged map groups on several streams.
 //
 // Requests that share a plan are merged along the map axis, so every stored
 // element of that plan's compressed operator is read once per group of up to
@@ -202,6 +204,26 @@ struct shtb_batch_s {
     int nstages = 0, warps = 4, grid = 0;
     size_t smem = 0;
     std::vector<void *> sched_allocs;
+    // stage-kernel schedule: per plan group the merged a_lm and pointer
+    // tables, per map group its u buffers and q^t, and the stream it runs on
+    int mode = 0;                     // 0 persistent kernel, 1 stage-kernel graph
+    int nstreams = 1;
+    struct GMapGroup {
+        int b0, nb, stream;
+        double *u0, *u1, *qt;
+        double cost;
+    };
+    struct GPlanGroup {
+        shtb_plan_s *plan;
+        int nmaps;
+        double2 *ai;
+        const double2 *const *alm_tab;
+        double *const *map_tab;
+        std::vector<GMapGroup> mgs;
+    };
+    std::vector<GPlanGroup> gg;
+    std::vector<cudaStream_t> side;   // streams 1 .. nstreams-1 (stream 0 is the caller's)
+    std::vector<cudaEvent_t> fork_join;
     // graph
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -228,6 +250,9 @@ void free_schedule(shtb_batch_s *b)
 {
     for (void *p : b->sched_allocs) cudaFree(p);
     b->sched_allocs.clear();
+    b->gg.clear();
+    b->dev = BatchDev{};
+    b->nstages = 0;
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -240,6 +265,7 @@ void free_schedule(shtb_batch_s *b)
 int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
 {
     free_schedule(b);
+    b->mode = 0;
     std::vector<BatchGroupDev> gdev(b->groups.size());
     std::vector<BatchMG> mgs;
     std::vector<int> mg_base(b->groups.size());
@@ -376,8 +402,104 @@ int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
     return SHTB_OK;
 }
 
+// Stage-kernel schedule: the stand-alone stage kernels over merged map
+// groups of up to `width` maps (residual blocks, butterfly levels, ring
+// FFTs writing each map through its pointer), the map groups spread over
+// `nstreams` streams by decreasing work so that small plans overlap big ones.
+int build_graph_schedule(shtb_batch_s *b, int width, int nstreams)
+{
+    free_schedule(b);
+    b->mode = 1;
+    b->nstreams = nstreams;
+    int rc;
+    void *d;
+    std::vector<std::pair<double, std::pair<int, int>>> order;   // (cost, (group, map group))
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        auto &G = b->groups[g];
+        shtb_plan_s *p = G.plan;
+        const BfPlanDev &bf = *p->bf;
+        shtb_batch_s::GPlanGroup P{};
+        P.plan = p;
+        P.nmaps = G.nmaps;
+        if ((rc = balloc(b->sched_allocs, &d, sizeof(double2) * (size_t)p->nalm * G.nmaps))) return rc;
+        P.ai = (double2 *)d;
+        if ((rc = balloc(b->sched_allocs, &d, sizeof(void *) * G.nmaps, G.alm_of_map.data()))) return rc;
+        P.alm_tab = (const double2 *const *)d;
+        if ((rc = balloc(b->sched_allocs, &d, sizeof(void *) * G.nmaps, G.map_of_map.data()))) return rc;
+        P.map_tab = (double *const *)d;
+        const double per_map = 4.0 * (double)(bf.n_dense + bf.n_r) + 2.0 * (double)bf.n_ident +
+                               p->stats.phi_flops_per_map;
+        for (int b0 = 0; b0 < G.nmaps;) {
+            const int left = G.nmaps - b0;
+            int nb = 1;
+            while (nb * 2 <= std::min(left, width)) nb *= 2;
+            shtb_batch_s::GMapGroup M{};
+            M.b0 = b0;
+            M.nb = nb;
+            M.cost = per_map * nb;
+            const size_t entry = sizeof(double) * 2 * nb;
+            if ((rc = balloc(b->sched_allocs, &d, entry * (size_t)bf.u_entries))) return rc;
+            M.u0 = (double *)d;
+            if ((rc = balloc(b->sched_allocs, &d, entry * (size_t)bf.u_entries))) return rc;
+            M.u1 = (double *)d;
+            if ((rc = balloc(b->sched_allocs, &d, entry * (size_t)bf.qt_entries))) return rc;
+            M.qt = (double *)d;
+            order.push_back({M.cost, {(int)g, (int)P.mgs.size()}});
+            P.mgs.push_back(M);
+            b0 += nb;
+        }
+        b->gg.push_back(std::move(P));
+    }
+    // longest processing time first onto the least loaded stream
+    std::sort(order.begin(), order.end(), [](const auto &a, const auto &c) { return a.first > c.first; });
+    std::vector<double> load(nstreams, 0.0);
+    for (auto &o : order) {
+        const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[s] += o.first;
+        b->gg[o.second.first].mgs[o.second.second].stream = s;
+    }
+    while ((int)b->side.size() < nstreams - 1) {
+        cudaStream_t s2;
+        SHTB_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        b->side.push_back(s2);
+    }
+    while ((int)b->fork_join.size() < nstreams) {
+        cudaEvent_t e;
+        SHTB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->fork_join.push_back(e);
+    }
+    b->warps = 0;
+    b->grid = 0;
+    return SHTB_OK;
+}
+
+int enqueue_graph(shtb_batch_s *b, cudaStream_t st)
+{
+    int rc;
+    for (auto &P : b->gg)
+        if ((rc = launch_bf_gather(P.plan, P.alm_tab, P.ai, P.nmaps, st))) return rc;
+    // fork: every side stream starts after the gathers
+    SHTB_CUDA_TRY(cudaEventRecord(b->fork_join[0], st));
+    for (int s = 1; s < b->nstreams; ++s) SHTB_CUDA_TRY(cudaStreamWaitEvent(b->side[s - 1], b->fork_join[0], 0));
+    for (auto &P : b->gg) {
+        for (auto &M : P.mgs) {
+            cudaStream_t ss = M.stream == 0 ? st : b->side[M.stream - 1];
+            if ((rc = launch_bf_legendre_group(P.plan, P.ai, P.nmaps, M.b0, M.nb, M.u0, M.u1, M.qt, ss)))
+                return rc;
+            if ((rc = launch_phi_synth_qt_ptr(P.plan, M.qt, M.nb, P.map_tab, M.b0, ss))) return rc;
+        }
+    }
+    // join
+    for (int s = 1; s < b->nstreams; ++s) {
+        SHTB_CUDA_TRY(cudaEventRecord(b->fork_join[s], b->side[s - 1]));
+        SHTB_CUDA_TRY(cudaStreamWaitEvent(st, b->fork_join[s], 0));
+    }
+    return SHTB_OK;
+}
+
 int enqueue(shtb_batch_s *b, cudaStream_t st)
 {
+    if (b->mode == 1) return enqueue_graph(b, st);
     SHTB_CUDA_TRY(cudaMemsetAsync(b->dev.done, 0, sizeof(int) * (b->nstages + 2), st));
     batch_kernel<<<b->grid, 32 * b->warps, b->smem, st>>>(b->dev);
     SHTB_CUDA_TRY(cudaGetLastError());
@@ -387,8 +509,10 @@ int enqueue(shtb_batch_s *b, cudaStream_t st)
 int read_status(shtb_batch_s *b, cudaStream_t st)
 {
     int err = 0;
-    SHTB_CUDA_TRY(cudaMemcpyAsync(&err, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (b->mode == 0)
+        SHTB_CUDA_TRY(cudaMemcpyAsync(&err, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SHTB_CUDA_TRY(cudaStreamSynchronize(st));
+    SHTB_CUDA_TRY(cudaGetLastError());
     if (err) return shtb_fail(SHTB_ETIMEOUT, "batch kernel: a stage wait gave up (error flag set)");
     return SHTB_OK;
 }
@@ -423,6 +547,8 @@ int shtb_batch_opts_init(shtb_batch_opts *o)
     o->group_width = 8;
     o->lpt = 1;
     o->spin_limit = 0;
+    o->schedule = 0;
+    o->streams = 0;
     return SHTB_OK;
 }
 
@@ -482,22 +608,33 @@ int shtb_batch_create(const shtb_request *reqs, int nreq, const shtb_batch_opts 
     const int w0 = b->opts.warps_per_block > 0 ? b->opts.warps_per_block : 4;
     const int gw = b->opts.group_width > 0 ? b->opts.group_width : 8;
     if (b->opts.autotune) {
-        // autotuner: warps per block x work order, timed on this batch
+        // autotuner, timed on this batch: the persistent kernel (warps per
+        // block x work order) and the stage-kernel graph (streams)
         double best = 1e30;
-        int bw = w0, bl = b->opts.lpt;
+        int bw = w0, bl = b->opts.lpt, bs = 0, bn = 1;
         for (int warps : {4, 8}) {
             for (int lpt : {1, 0}) {
                 if ((rc = build_schedule(b, warps, gw, lpt))) { shtb_batch_destroy(b); return rc; }
                 const double ms = time_schedule(b, st, 2);
-                if (ms < best) { best = ms; bw = warps; bl = lpt; }
+                if (ms < best) { best = ms; bw = warps; bl = lpt; bs = 0; }
             }
+        }
+        for (int ns : {1, 2, 4, 8}) {
+            if ((rc = build_graph_schedule(b, gw, ns))) { shtb_batch_destroy(b); return rc; }
+            const double ms = time_schedule(b, st, 2);
+            if (ms < best) { best = ms; bs = 1; bn = ns; }
         }
         b->opts.warps_per_block = bw;
         b->opts.lpt = bl;
+        b->opts.schedule = bs;
+        b->opts.streams = bn;
         b->tuned_ms = best;
     }
-    if ((rc = build_schedule(b, b->opts.warps_per_block > 0 ? b->opts.warps_per_block : w0, gw,
-                             b->opts.lpt))) {
+    if (b->opts.schedule == 1)
+        rc = build_graph_schedule(b, gw, b->opts.streams > 0 ? b->opts.streams : 4);
+    else
+        rc = build_schedule(b, b->opts.warps_per_block > 0 ? b->opts.warps_per_block : w0, gw, b->opts.lpt);
+    if (rc) {
         shtb_batch_destroy(b);
         return rc;
     }
@@ -544,8 +681,17 @@ int shtb_batch_info(shtb_batch b, int *warps_per_block, int *grid, int *npacks, 
     return SHTB_OK;
 }
 
+int shtb_batch_schedule(shtb_batch b, int *schedule, int *streams)
+{
+    if (!b) return shtb_fail(SHTB_EINVAL, "batch is NULL");
+    if (schedule) *schedule = b->mode;
+    if (streams) *streams = b->mode == 1 ? b->nstreams : 0;
+    return SHTB_OK;
+}
+
 int shtb_test_batch_stall(shtb_batch b, int on)
 {
+    if (b && b->mode != 0) return shtb_fail(SHTB_ENOTSUP, "stage waits exist in the persistent schedule only");
     if (!b || b->nstages < 2) return shtb_fail(SHTB_EINVAL, "batch is NULL or empty");
     int t0 = 0;
     SHTB_CUDA_TRY(cudaMemcpy(&t0, b->dev.stage_total, sizeof(int), cudaMemcpyDeviceToHost));
@@ -561,6 +707,8 @@ int shtb_batch_destroy(shtb_batch b)
     if (!b) return SHTB_OK;
     free_schedule(b);
     for (void *p : b->allocs) cudaFree(p);
+    for (cudaStream_t s2 : b->side) cudaStreamDestroy(s2);
+    for (cudaEvent_t e : b->fork_join) cudaEventDestroy(e);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
     return SHTB_OK;

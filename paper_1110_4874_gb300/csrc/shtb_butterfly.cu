@@ -73,27 +73,26 @@ bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, 
                                        sout + (size_t)wib * maxnc * OS, lane);
 }
 
-// One map group: residual blocks, butterfly levels, then (map != nullptr)
-// the ring stage.  With map == nullptr the group's q^t is the caller's
-// array (the Legendre stage alone).
+// residual blocks of one map group (maps b0 .. b0+NB-1 of ai)
 template <int NB>
-int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
-              double *qt, double *map, cudaStream_t st)
+int launch_r(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
+             double *qt, cudaStream_t st)
 {
     const BfPlanDev &bf = *p->bf;
-    const PlanView &v = p->view;
-    shtb_plan_s *pp = const_cast<shtb_plan_s *>(p);
-    const int ev_leg = profile_begin(pp, st);
-    int ev = profile_begin(pp, st);
-    if (bf.n_ritems > 0) {
-        const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
-        bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(v, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
-                                                        nmaps, b0, u0, u1, bf.depth_parity, qt);
-        SHTB_CUDA_TRY(cudaGetLastError());
-        ++p->launches;
-    }
-    profile_end(pp, st, 5, ev);
-    ev = profile_begin(pp, st);
+    if (bf.n_ritems == 0) return SHTB_OK;
+    const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
+    bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(p->view, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
+                                                    nmaps, b0, u0, u1, bf.depth_parity, qt);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    return SHTB_OK;
+}
+
+// butterfly levels of one map group, top down; level 1 writes q^t
+template <int NB>
+int launch_levels(const shtb_plan_s *p, double *u0, double *u1, double *qt, cudaStream_t st)
+{
+    const BfPlanDev &bf = *p->bf;
     for (int lev = bf.depth_max; lev >= 1; --lev) {
         const int n = bf.level_counts[lev - 1];
         if (n == 0) continue;
@@ -110,16 +109,49 @@ int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
+    return SHTB_OK;
+}
+
+// One map group: residual blocks, butterfly levels, then (map != nullptr)
+// the ring stage.  With map == nullptr the group's q^t is the caller's
+// array (the Legendre stage alone).
+template <int NB>
+int run_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
+              double *qt, double *map, cudaStream_t st)
+{
+    shtb_plan_s *pp = const_cast<shtb_plan_s *>(p);
+    const int ev_leg = profile_begin(pp, st);
+    int ev = profile_begin(pp, st);
+    int rc = launch_r<NB>(p, ai, nmaps, b0, u0, u1, qt, st);
+    if (rc) return rc;
+    profile_end(pp, st, 5, ev);
+    ev = profile_begin(pp, st);
+    if ((rc = launch_levels<NB>(p, u0, u1, qt, st))) return rc;
     profile_end(pp, st, 6, ev);
     profile_end(pp, st, 0, ev_leg);
     if (!map) return SHTB_OK;
     // ring stage of this group straight from q^0, q^1 (parity combine fused)
     ev = profile_begin(pp, st);
-    int rc = launch_phi_synth_qt(p, qt, NB, map, b0, st);
+    rc = launch_phi_synth_qt(p, qt, NB, map, b0, st);
     profile_end(pp, st, 1, ev);
     return rc;
 }
 
+// a_lm of merged maps (one device pointer per map) into ai[idx][map]
+__global__ void bf_gather_kernel(PlanView v, const double2 *const *__restrict__ alm_of_map,
+                                 double2 *__restrict__ ai, int nmaps)
+{
+    const int m = blockIdx.x;
+    const int L = v.lmax;
+    const long long off = shtb_dev::alm_off(L, m);
+    const int n = L - m + 1;
+    for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {
+        const int b = i / n, dl = i - b * n;
+        const long long idx = off + dl;
+        const double2 a = alm_of_map[b][idx];
+        ai[(size_t)idx * nmaps + b] = make_double2(a.x, m == 0 ? 0.0 : a.y);
+    }
+}
 
 // ------------------------------------------------------------------ adjoint
 // a^t = Lambda g^t: the transposed butterfly.  Level items run bottom-up:
@@ -341,4 +373,30 @@ int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, voi
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     return SHTB_OK;
+}
+
+int launch_bf_gather(const shtb_plan_s *p, const double2 *const *alm_of_map, double2 *ai, int nmaps,
+                     cudaStream_t st)
+{
+    bf_gather_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm_of_map, ai, nmaps);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    return SHTB_OK;
+}
+
+int launch_bf_legendre_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, int nb, double *u0,
+                             double *u1, double *qt, cudaStream_t st)
+{
+    int rc;
+    switch (nb) {
+    case 8: if ((rc = launch_r<8>(p, ai, nmaps, b0, u0, u1, qt, st))) return rc;
+            return launch_levels<8>(p, u0, u1, qt, st);
+    case 4: if ((rc = launch_r<4>(p, ai, nmaps, b0, u0, u1, qt, st))) return rc;
+            return launch_levels<4>(p, u0, u1, qt, st);
+    case 2: if ((rc = launch_r<2>(p, ai, nmaps, b0, u0, u1, qt, st))) return rc;
+            return launch_levels<2>(p, u0, u1, qt, st);
+    case 1: if ((rc = launch_r<1>(p, ai, nmaps, b0, u0, u1, qt, st))) return rc;
+            return launch_levels<1>(p, u0, u1, qt, st);
+    default: return shtb_fail(SHTB_EINVAL, "map group width must be 1, 2, 4 or 8");
+    }
 }

@@ -174,6 +174,9 @@ int launch_phi_adjoint(const shtb_plan_s *p, const double *map, double2 *q, int 
                        cudaStream_t st);
 int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0,
                         cudaStream_t st);
+// ... writing map b0 + b to map_of_map[b0 + b] (device array of map pointers)
+int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, double *const *map_of_map,
+                            int b0, cudaStream_t st);
 
 // shtb_butterfly.cu
 size_t bf_workspace_bytes(const shtb_plan_s *p);
@@ -182,6 +185,13 @@ size_t bf_workspace_bytes(const shtb_plan_s *p);
 int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
                     int nmaps, cudaStream_t st, double *qt_out = nullptr);
 void bf_release(shtb_plan_s *p);
+// batched serving (stage-kernel schedule): a_lm of merged maps, given one
+// device pointer per map, into ai[idx][map]; residual blocks + butterfly
+// levels of maps b0 .. b0+nb-1 of ai (nb = 1, 2, 4, 8) into that group's q^t
+int launch_bf_gather(const shtb_plan_s *p, const double2 *const *alm_of_map, double2 *ai, int nmaps,
+                     cudaStream_t st);
+int launch_bf_legendre_group(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, int nb, double *u0,
+                             double *u1, double *qt, cudaStream_t st);
 int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
                       int nmaps, cudaStream_t st);
 

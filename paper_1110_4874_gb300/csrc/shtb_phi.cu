@@ -41,16 +41,22 @@ phi_synth_kernel(PlanView v, const int *__restrict__ rings, const double2 *__res
 
 // ring stage of a compressed plan's map group, straight from the parity
 // halves q^0, q^1 of the butterfly output (no separate combine pass)
+// maps: either stacked at map + (b0 + b) npix, or one pointer per map
+struct MapOut {
+    double *map;
+    double *const *table;
+};
+
 template <int KIND>
 __global__ void __launch_bounds__(kPhiThreads)
 phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ qt,
-                    double *__restrict__ map, int b0)
+                    MapOut mo, int b0)
 {
     extern __shared__ double2 sm[];
     const int ring = rings[blockIdx.x];
     const int b = blockIdx.y;
-    shtb_dev::phi_synth_ring_qt<KIND, false>(v, ring, qt, b,
-                                             map + (size_t)(b0 + b) * v.npix + v.ring_start[ring], sm);
+    double *base = mo.table ? mo.table[b0 + b] : mo.map + (size_t)(b0 + b) * v.npix;
+    shtb_dev::phi_synth_ring_qt<KIND, false>(v, ring, qt, b, base + v.ring_start[ring], sm);
 }
 
 template <int KIND>
@@ -148,7 +154,7 @@ int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int 
 }
 
 template <int KIND>
-int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, double *map, int b0, cudaStream_t st)
+int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0, cudaStream_t st)
 {
     const RingSet rs = ring_set(p, KIND);
     if (rs.n == 0) return SHTB_OK;
@@ -162,16 +168,27 @@ int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, double *map,
     return SHTB_OK;
 }
 
+int launch_qt_all(const shtb_plan_s *p, const double *qt, int nb, MapOut mo, int b0, cudaStream_t st)
+{
+    const double2 *q2 = (const double2 *)qt;
+    int rc;
+    if ((rc = launch_qt_kind<kBluestein>(p, q2, nb, mo, b0, st))) return rc;
+    if ((rc = launch_qt_kind<kDirect>(p, q2, nb, mo, b0, st))) return rc;
+    return launch_qt_kind<kDirectBig>(p, q2, nb, mo, b0, st);
+}
+
 }  // namespace
 
 int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0,
                         cudaStream_t st)
 {
-    const double2 *q2 = (const double2 *)qt;
-    int rc;
-    if ((rc = launch_qt_kind<kBluestein>(p, q2, nb, map, b0, st))) return rc;
-    if ((rc = launch_qt_kind<kDirect>(p, q2, nb, map, b0, st))) return rc;
-    return launch_qt_kind<kDirectBig>(p, q2, nb, map, b0, st);
+    return launch_qt_all(p, qt, nb, MapOut{map, nullptr}, b0, st);
+}
+
+int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, double *const *map_of_map,
+                            int b0, cudaStream_t st)
+{
+    return launch_qt_all(p, qt, nb, MapOut{nullptr, map_of_map}, b0, st);
 }
 
 int launch_phi_synth(const shtb_plan_s *p, const double2 *q, double *map, int nmaps, cudaStream_t st)

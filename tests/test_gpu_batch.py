@@ -43,7 +43,11 @@ def test_batch_equals_plain_requests(setup):
     plans, reqs = setup
     batch = sh.shtb_batch_create(reqs, autotune=True)
     info = sh.shtb_batch_info(batch)
-    assert info["warps_per_block"] in (4, 8) and info["grid"] > 0 and info["npacks"] > 0
+    assert info["schedule"] in (0, 1) and info["tuned_ms"] > 0
+    if info["schedule"] == 0:
+        assert info["warps_per_block"] in (4, 8) and info["grid"] > 0 and info["npacks"] > 0
+    else:
+        assert info["streams"] in (1, 2, 4, 8)
     torch.cuda.synchronize()
     first = None
     for it in range(2):          # first run captures the graph, second replays it
@@ -70,6 +74,31 @@ def test_batch_on_a_user_stream(setup):
     sh.shtb_batch_status(batch, s)
     for p, alm, maps in reqs[:4]:
         assert same_map(maps, p.synthesize(alm))
+    sh.shtb_batch_destroy(batch)
+
+
+@pytest.mark.parametrize("streams", [1, 3])
+def test_stage_kernel_schedule(setup, streams):
+    """The stage-kernel graph schedule (stand-alone kernels over merged map
+    groups, spread over streams): same maps as the single-request path to
+    rounding, and a graph replay repeats the captured run bit for bit."""
+    plans, reqs = setup
+    batch = sh.shtb_batch_create(reqs, autotune=False, schedule=1, streams=streams)
+    assert sh.shtb_batch_schedule(batch) == {"schedule": 1, "streams": streams}
+    first = None
+    for _ in range(2):
+        for _, _, maps in reqs:
+            maps.fill_(float("nan"))
+        sh.shtb_batch_run(batch)
+        sh.shtb_batch_status(batch)
+        if first is None:
+            first = [m.clone() for _, _, m in reqs]
+    for (p, alm, maps), f in zip(reqs, first):
+        assert torch.equal(maps, f)
+        assert same_map(maps, p.synthesize(alm))
+    with pytest.raises(sh.ShtbError) as e:
+        sh.shtb_test_batch_stall(batch, True)
+    assert e.value.code == sh.SHTB_ENOTSUP
     sh.shtb_batch_destroy(batch)
 
 
