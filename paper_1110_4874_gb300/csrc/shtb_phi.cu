@@ -25,10 +25,17 @@ namespace {
 
 using namespace shtb_dev;
 
-constexpr int kPhiThreads = 256;
+// threads per ring CTA: the Bluestein variant holds up to ~8.4k complex
+// values of shared memory per CTA (one CTA per SM at the longest rings), so
+// it runs twice the threads to keep the FP64 pipe fed
+template <int KIND>
+constexpr int phi_threads()
+{
+    return KIND == kBluestein ? 512 : 256;
+}
 
 template <int KIND>
-__global__ void __launch_bounds__(kPhiThreads)
+__global__ void __launch_bounds__(phi_threads<KIND>())
 phi_synth_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ q,
                  double *__restrict__ map)
 {
@@ -48,7 +55,7 @@ struct MapOut {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(kPhiThreads)
+__global__ void __launch_bounds__(phi_threads<KIND>())
 phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ qt,
                     MapOut mo, int b0)
 {
@@ -60,7 +67,7 @@ phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kPhiThreads)
+__global__ void __launch_bounds__(phi_threads<KIND>())
 phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__restrict__ map,
                    double2 *__restrict__ qa)
 {
@@ -131,12 +138,12 @@ int launch_kind(const shtb_plan_s *p, bool synth, const void *in, void *out, int
     if (synth) {
         SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
-        phi_synth_kernel<KIND><<<grid, kPhiThreads, smem, st>>>(p->view, rs.rings, (const double2 *)in,
+        phi_synth_kernel<KIND><<<grid, phi_threads<KIND>(), smem, st>>>(p->view, rs.rings, (const double2 *)in,
                                                                 (double *)out);
     } else {
         SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_adjoint_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
-        phi_adjoint_kernel<KIND><<<grid, kPhiThreads, smem, st>>>(p->view, rs.rings, (const double *)in,
+        phi_adjoint_kernel<KIND><<<grid, phi_threads<KIND>(), smem, st>>>(p->view, rs.rings, (const double *)in,
                                                                   (double2 *)out);
     }
     SHTB_CUDA_TRY(cudaGetLastError());
@@ -161,7 +168,7 @@ int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, 
     const size_t smem = sizeof(double2) * (size_t)rs.len;
     SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    phi_synth_qt_kernel<KIND><<<dim3((unsigned)rs.n, (unsigned)nb), kPhiThreads, smem, st>>>(p->view, rs.rings,
+    phi_synth_qt_kernel<KIND><<<dim3((unsigned)rs.n, (unsigned)nb), phi_threads<KIND>(), smem, st>>>(p->view, rs.rings,
                                                                                             qt, map, b0);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
