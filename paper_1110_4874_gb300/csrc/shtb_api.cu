@@ -286,6 +286,10 @@ int shtb_plan_destroy(shtb_plan p)
     for (void *a : p->allocations) cudaFree(a);
     if (p->ws) cudaFree(p->ws);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->copy_stream) {
+        cudaStreamDestroy(p->copy_stream);
+        for (cudaEvent_t e : p->chunk_ev) cudaEventDestroy(e);
+    }
     bf_release(p);
     if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
     delete p;
@@ -330,9 +334,16 @@ int shtb_synthesize_host(shtb_plan p, const double *alm_host, double *map_host, 
     cudaStream_t st = (cudaStream_t)stream;
     Workspace w = carve(p, nmaps);
     SHTB_CUDA_TRY(cudaMemcpyAsync(w.alm, alm_host, alm_bytes(p, nmaps), cudaMemcpyHostToDevice, st));
-    if ((rc = run_synthesis(p, w.alm, w.map, nmaps, st))) return rc;
-    SHTB_CUDA_TRY(cudaMemcpyAsync(map_host, w.map, sizeof(double) * (size_t)nmaps * p->npix,
-                                  cudaMemcpyDeviceToHost, st));
+    if (p->bf) {
+        // compressed plans: the maps come back ring chunk by ring chunk,
+        // overlapping the rest of the ring stage
+        if (p->profiling) ++p->prof_calls;
+        if ((rc = launch_bf_synth_to_host(p, w.alm, w.ap, w.bf, w.map, map_host, nmaps, st))) return rc;
+    } else {
+        if ((rc = run_synthesis(p, w.alm, w.map, nmaps, st))) return rc;
+        SHTB_CUDA_TRY(cudaMemcpyAsync(map_host, w.map, sizeof(double) * (size_t)nmaps * p->npix,
+                                      cudaMemcpyDeviceToHost, st));
+    }
     SHTB_CUDA_TRY(cudaStreamSynchronize(st));
     return SHTB_OK;
 }

@@ -353,6 +353,48 @@ int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void 
     return SHTB_OK;
 }
 
+int launch_bf_synth_to_host(shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
+                            double *map_host, int nmaps, cudaStream_t st)
+{
+    constexpr int NCH = shtb_plan_s::kPhiChunks;
+    if (!p->copy_stream) {
+        SHTB_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        for (auto &e : p->chunk_ev) SHTB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const BfPlanDev &bf = *p->bf;
+    const size_t entry = 16;
+    double *u0 = (double *)ws;
+    double *u1 = u0 + (size_t)bf.u_entries * entry;
+    double *qt = u1 + (size_t)bf.u_entries * entry;
+    bf_interleave_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ai, nmaps);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    for (int b0 = 0; b0 < nmaps;) {
+        const int left = nmaps - b0;
+        const int nb = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        int rc = launch_bf_legendre_group(p, ai, nmaps, b0, nb, u0, u1, qt, st);
+        if (rc) return rc;
+        // ring stage chunk by chunk; each chunk's pixels go back while the
+        // next chunk (or the next map group) computes
+        for (int c = 0; c < NCH; ++c) {
+            if ((rc = launch_phi_synth_qt_chunk(p, qt, nb, map, b0, c, st))) return rc;
+            const long long p0 = p->chunk_pix[c], p1 = p->chunk_pix[c + 1];
+            if (p1 == p0) continue;
+            SHTB_CUDA_TRY(cudaEventRecord(p->chunk_ev[c], st));
+            SHTB_CUDA_TRY(cudaStreamWaitEvent(p->copy_stream, p->chunk_ev[c], 0));
+            for (int b = b0; b < b0 + nb; ++b)
+                SHTB_CUDA_TRY(cudaMemcpyAsync(map_host + (size_t)b * p->npix + p0, map + (size_t)b * p->npix + p0,
+                                              sizeof(double) * (size_t)(p1 - p0), cudaMemcpyDeviceToHost,
+                                              p->copy_stream));
+        }
+        b0 += nb;
+    }
+    // the caller's stream completes after the last copy
+    SHTB_CUDA_TRY(cudaEventRecord(p->chunk_ev[0], p->copy_stream));
+    SHTB_CUDA_TRY(cudaStreamWaitEvent(st, p->chunk_ev[0], 0));
+    return SHTB_OK;
+}
+
 int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
                       int nmaps, cudaStream_t st)
 {

@@ -112,6 +112,20 @@ struct shtb_plan_s {
     std::vector<int> direct_rings, blue_rings, big_rings;
     int max_K_direct = 0, max_M_mx = 0, max_K_big = 0;
     int *d_direct_rings = nullptr, *d_blue_rings = nullptr, *d_big_rings = nullptr;
+    // the rings cut into kPhiChunks runs of consecutive rings with about equal
+    // pixel counts, per run and ring variant a device list (chunk_list + off)
+    // and its longest transform; pixels [chunk_pix[c], chunk_pix[c+1]) of a
+    // map are written by run c (host-buffer synthesis overlaps their copy
+    // back with the next run)
+    static constexpr int kPhiChunks = 4;
+    struct ChunkKind {
+        int off, n, len;
+    };
+    ChunkKind chunk_kind[kPhiChunks][3] = {};
+    long long chunk_pix[kPhiChunks + 1] = {};
+    int *d_chunk_list = nullptr;
+    cudaStream_t copy_stream = nullptr;            // created on first use, owned
+    cudaEvent_t chunk_ev[kPhiChunks] = {};
     // largest radix-2 transform of the batch kernel (power-of-two K, or the
     // power-of-two Bluestein length)
     int max_K_pow2 = 0, max_M_blue = 0;
@@ -174,6 +188,9 @@ int launch_phi_adjoint(const shtb_plan_s *p, const double *map, double2 *q, int 
                        cudaStream_t st);
 int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0,
                         cudaStream_t st);
+// ... for the rings of chunk `chunk` only (shtb_plan_s::kPhiChunks runs)
+int launch_phi_synth_qt_chunk(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0, int chunk,
+                              cudaStream_t st);
 // ... writing map b0 + b to map_of_map[b0 + b] (device array of map pointers)
 int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, double *const *map_of_map,
                             int b0, cudaStream_t st);
@@ -184,6 +201,10 @@ size_t bf_workspace_bytes(const shtb_plan_s *p);
 // alone, q^t of map b written to qt_out + b [2][nhalf][L+1] complex
 int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
                     int nmaps, cudaStream_t st, double *qt_out = nullptr);
+// whole synthesis with the maps copied back to host memory as the ring
+// stage finishes each chunk of rings (the copies overlap the rest)
+int launch_bf_synth_to_host(shtb_plan_s *p, const double2 *alm, double2 *ai, void *ws, double *map,
+                            double *map_host, int nmaps, cudaStream_t st);
 void bf_release(shtb_plan_s *p);
 // batched serving (stage-kernel schedule): a_lm of merged maps, given one
 // device pointer per map, into ai[idx][map]; residual blocks + butterfly

@@ -175,6 +175,21 @@ int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, 
     return SHTB_OK;
 }
 
+template <int KIND>
+int launch_qt_list(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0, const int *rings,
+                   int n, int len, cudaStream_t st)
+{
+    if (n == 0) return SHTB_OK;
+    const size_t smem = sizeof(double2) * (size_t)len;
+    SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    phi_synth_qt_kernel<KIND><<<dim3((unsigned)n, (unsigned)nb), phi_threads<KIND>(), smem, st>>>(p->view, rings,
+                                                                                                 qt, map, b0);
+    SHTB_CUDA_TRY(cudaGetLastError());
+    ++p->launches;
+    return SHTB_OK;
+}
+
 int launch_qt_all(const shtb_plan_s *p, const double *qt, int nb, MapOut mo, int b0, cudaStream_t st)
 {
     const double2 *q2 = (const double2 *)qt;
@@ -190,6 +205,20 @@ int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *
                         cudaStream_t st)
 {
     return launch_qt_all(p, qt, nb, MapOut{map, nullptr}, b0, st);
+}
+
+int launch_phi_synth_qt_chunk(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0, int chunk,
+                              cudaStream_t st)
+{
+    const double2 *q2 = (const double2 *)qt;
+    const MapOut mo{map, nullptr};
+    const auto *ck = p->chunk_kind[chunk];
+    int rc;
+    if ((rc = launch_qt_list<kBluestein>(p, q2, nb, mo, b0, p->d_chunk_list + ck[1].off, ck[1].n, ck[1].len, st)))
+        return rc;
+    if ((rc = launch_qt_list<kDirect>(p, q2, nb, mo, b0, p->d_chunk_list + ck[0].off, ck[0].n, ck[0].len, st)))
+        return rc;
+    return launch_qt_list<kDirectBig>(p, q2, nb, mo, b0, p->d_chunk_list + ck[2].off, ck[2].n, ck[2].len, st);
 }
 
 int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, double *const *map_of_map,

@@ -156,6 +156,16 @@ __device__ __forceinline__ void dft_small(double2 (&a)[R])
     }
 }
 
+// s = a + w b, d = a - w b as s and 2a - s: six FP64 instructions (four
+// fused multiply-adds, two for d) instead of a complex product and two sums
+__device__ __forceinline__ void bfly_fma(double2 a, double2 b, double2 w, double2 &s, double2 &d)
+{
+    s.x = fma(w.x, b.x, fma(-w.y, b.y, a.x));
+    s.y = fma(w.x, b.y, fma(w.y, b.x, a.y));
+    d.x = fma(2.0, a.x, -s.x);
+    d.y = fma(2.0, a.y, -s.y);
+}
+
 // one pass of radix R over N points in blocks of B; tw(t) = e^{2 pi i t / N}
 template <int R, bool INV, class TW>
 __device__ __forceinline__ void mx_pass(double2 *x, int N, int B, const TW &tw)
@@ -166,7 +176,24 @@ __device__ __forceinline__ void mx_pass(double2 *x, int N, int B, const TW &tw)
         double2 a[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) a[q] = x[base + q * Ns];
-        if (INV) {
+        if constexpr (INV && R == 2) {
+            // y_0,1 = a_0 +- w a_1, w = w_B^j
+            double2 y0, y1;
+            bfly_fma(a[0], a[1], tw(j * step), y0, y1);
+            a[0] = y0;
+            a[1] = y1;
+        } else if constexpr (INV && R == 4) {
+            // twiddles w_B^{pj} then the 4-point DFT (exponent +1), as two
+            // layers of fused radix-2 butterflies: u0 = a0 +- w2 a2,
+            // u1 = a1 +- w2 a3 (w2 = w_B^{2j}), then y_0,2 = u0+ +- w1 u1+,
+            // y_1,3 = u0- +- i w1 u1- (w1 = w_B^j)
+            const double2 w1 = tw(j * step), w2 = tw(2 * j * step);
+            double2 u0p, u0m, u1p, u1m;
+            bfly_fma(a[0], a[2], w2, u0p, u0m);
+            bfly_fma(a[1], a[3], w2, u1p, u1m);
+            bfly_fma(u0p, u1p, w1, a[0], a[2]);
+            bfly_fma(u0m, u1m, make_double2(-w1.y, w1.x), a[1], a[3]);
+        } else if (INV) {
             if (j) {
 #pragma unroll
                 for (int p = 1; p < R; ++p) a[p] = cmul(a[p], tw(p * j * step));

@@ -581,7 +581,7 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     // Mixed-radix tables of the stand-alone ring kernels: K factoring over
     // 2, 3, 5, 7, 11, 13 -> direct transform of length K; otherwise Bluestein
     // through the smallest 7-smooth length M >= 2K - 1.
-    std::vector<int> rad, ring_rad(p->nrings), ring_mx(p->nrings, 0);
+    std::vector<int> rad, ring_rad(p->nrings), ring_mx(p->nrings, 0), chunk_list;
     std::vector<long long> ring_mfb(p->nrings, 0), ring_mtw(p->nrings, 0);
     std::vector<double2> mfb, mtw;
     {
@@ -672,6 +672,33 @@ int shtb_build_dense_plan(shtb_plan_s *p)
                          [&](int a, int b) { return p->ring_J[a] > p->ring_J[b]; });
         std::stable_sort(p->blue_rings.begin(), p->blue_rings.end(),
                          [&](int a, int b) { return ring_mx[a] > ring_mx[b]; });
+        // chunks of consecutive rings with about equal pixel counts
+        constexpr int NCH = shtb_plan_s::kPhiChunks;
+        std::vector<int> chunk_of(p->nrings);
+        {
+            int c = 0;
+            for (int r = 0; r < p->nrings; ++r) {
+                while (c < NCH - 1 && p->ring_start[r] >= (c + 1) * p->npix / NCH) ++c;
+                chunk_of[r] = c;
+            }
+            for (int cc = 0; cc <= NCH; ++cc) p->chunk_pix[cc] = cc == NCH ? p->npix : -1;
+            for (int r = p->nrings - 1; r >= 0; --r) p->chunk_pix[chunk_of[r]] = p->ring_start[r];
+            for (int cc = NCH - 1; cc >= 0; --cc)       // an empty chunk starts where the next one does
+                if (p->chunk_pix[cc] < 0) p->chunk_pix[cc] = p->chunk_pix[cc + 1];
+        }
+        const std::vector<int> *lists[3] = {&p->direct_rings, &p->blue_rings, &p->big_rings};
+        for (int cc = 0; cc < NCH; ++cc)
+            for (int k = 0; k < 3; ++k) {
+                auto &ck = p->chunk_kind[cc][k];
+                ck.off = (int)chunk_list.size();
+                ck.len = 0;
+                for (int r : *lists[k])
+                    if (chunk_of[r] == cc) {
+                        chunk_list.push_back(r);
+                        ck.len = std::max(ck.len, k == 1 ? ring_mx[r] : p->ring_J[r] / 2);
+                    }
+                ck.n = (int)chunk_list.size() - ck.off;
+            }
     }
 
     // algorithmic FFT flops: 2.5 J log2 J per real ring transform of length J
@@ -729,6 +756,9 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     rc = plan_alloc_upload(p, &d, p->big_rings.data(), sizeof(int) * p->big_rings.size());
     if (rc) return rc;
     p->d_big_rings = (int *)d;
+    rc = plan_alloc_upload(p, &d, chunk_list.data(), sizeof(int) * chunk_list.size());
+    if (rc) return rc;
+    p->d_chunk_list = (int *)d;
 
     // bytes one call reads from the plan (Legendre tables + start values)
     p->stats.plan_read_bytes = (long long)(sizeof(RecCoef) * coef.size() + sizeof(int) * jstart.size() +
