@@ -143,9 +143,14 @@ __device__ __forceinline__ void bf_dense_pass(int k, int nd, const double *__res
                                               int c, double *out)
 {
     constexpr int C = 2 * NB, LD = Lanes<C>::LD, OS = out_stride<C>();
+    // each row's dot product starts from its scratch entry (0, or the other
+    // child's contribution), so no separate add is needed afterwards
     double acc[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    for (int r = 0; r < NR; ++r) {
+        const int d = q0 + dl + r * LD;
+        acc[r] = d < nd ? out[dpos[d] * OS + c] : 0.0;
+    }
     const double *__restrict__ Tq = T + q0 + dl;
 #pragma unroll 2
     for (int i = 0; i < k; ++i) {
@@ -160,7 +165,7 @@ __device__ __forceinline__ void bf_dense_pass(int k, int nd, const double *__res
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int d = q0 + dl + r * LD;
-        if (d < nd) out[dpos[d] * OS + c] += acc[r];
+        if (d < nd) out[dpos[d] * OS + c] = acc[r];
     }
 }
 
@@ -202,10 +207,13 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf
             const int nr = min(NRMAX, (nd - q0 + LD - 1) / LD);
             bf_dense_dispatch<NB, NRMAX, CG>(nr, k, nd, T, dpos, u + c, q0, dl, c, out);
         }
+        // identity entries: the first child's land on zeroed scratch (a store),
+        // the second child's on whatever the first child left there
         const int *__restrict__ ipos = ints + it.ipos_off[s];
         for (int x = lane; x < k * C; x += 32) {
             const int i = x / C, cc = x - i * C;
-            out[ipos[i] * OS + cc] += ldp<CG>(u + x);
+            double *o = out + ipos[i] * OS + cc;
+            *o = s ? *o + ldp<CG>(u + x) : ldp<CG>(u + x);
         }
         __syncwarp();
     }
