@@ -158,6 +158,55 @@ __global__ void bf_gather_kernel(PlanView v, const double2 *const *__restrict__ 
 // item (parent P, group G) gathers its candidate vector (g on a leaf block at
 // level 1, else the u of level l-1) and applies both children's T:
 // u_s = [I | T_s] v  (identity entries copy, dense rows are k x nd dots).
+
+// NR rows of child s per lane, rows q0 + dl + r LD (r < NR), component c
+template <int NB, int NR>
+__device__ __forceinline__ void adj_rows(const BfItem &it, int s, const int *__restrict__ ints,
+                                         const double *__restrict__ dbl, const double *in, int q0, int dl,
+                                         int c, double *__restrict__ uout)
+{
+    constexpr int C = 2 * NB, LD = shtb_dev::Lanes<C>::LD;
+    const int k = it.k[s], nd = it.nd[s];
+    const double *__restrict__ T = dbl + it.T_off[s];        // k x nd, row-major
+    const int *__restrict__ dpos = ints + it.dpos_off[s];
+    const int *__restrict__ ipos = ints + it.ipos_off[s];
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = q0 + dl + r * LD;
+        acc[r] = i < k ? in[ipos[i] * C + c] : 0.0;
+    }
+#pragma unroll 2
+    for (int d = 0; d < nd; ++d) {
+        const double x = in[dpos[d] * C + c];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int i = q0 + dl + r * LD;
+            const double t = i < k ? T[(size_t)i * nd + d] : 0.0;
+            acc[r] = fma(t, x, acc[r]);
+        }
+    }
+    double *dst = uout + (size_t)it.u_off[s] * C + c;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int i = q0 + dl + r * LD;
+        if (i < k) dst[(size_t)i * C] = acc[r];
+    }
+}
+
+template <int NB, int NR>
+__device__ __forceinline__ void adj_rows_dispatch(int nr, const BfItem &it, int s, const int *ints,
+                                                  const double *dbl, const double *in, int q0, int dl, int c,
+                                                  double *uout)
+{
+    if constexpr (NR > 1) {
+        if (nr < NR) {
+            adj_rows_dispatch<NB, NR - 1>(nr, it, s, ints, dbl, in, q0, dl, c, uout);
+            return;
+        }
+    }
+    adj_rows<NB, NR>(it, s, ints, dbl, in, q0, dl, c, uout);
+}
 template <int NB>
 __global__ void __launch_bounds__(32 * kBfWarps)
 bf_adj_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__restrict__ ints,
@@ -185,43 +234,76 @@ bf_adj_level_kernel(const BfItem *__restrict__ items, int nitems, const int *__r
         for (int i = lane; i < it.nc * C; i += 32) in[i] = src[i];
     }
     __syncwarp();
-    // rows of both children's u as one list of k0 + k1 rows: identity entry
-    // plus a dot product of the row of T with the candidates' dense part
-    using Tl = Tile<C>;
-    const int il = lane % Tl::LD, cg = lane / Tl::LD;
-    const int k0 = it.k[0], kt = it.k[0] + it.k[1];
-    const int ndmax = max(it.nd[0], it.nd[1]);
-    for (int q0 = 0; q0 < kt; q0 += Tl::LD) {
-        const int q = q0 + il;
-        const bool valid = q < kt;
-        const int s = (valid && q >= k0) ? 1 : 0;
-        const int i = s ? q - k0 : (valid ? q : 0);
-        const int nd = s ? it.nd[1] : it.nd[0];
-        const double *__restrict__ Ti = dbl + (s ? it.T_off[1] : it.T_off[0]) + (size_t)i * nd;
-        const int *__restrict__ dpos = ints + (s ? it.dpos_off[1] : it.dpos_off[0]);
-        const int *__restrict__ ipos = ints + (s ? it.ipos_off[1] : it.ipos_off[0]);
-        double acc[Tl::CPL];
-        const double *xi = in + (valid ? ipos[i] : 0) * C + cg * Tl::CPL;
+    // each child in turn, its k rows over the lanes (one component per lane,
+    // an exact per-lane row count): identity entry plus a dot product of the
+    // row of T with the candidates' dense part
+    using shtb_dev::Lanes;
+    constexpr int LD = Lanes<C>::LD, NRMAX = Lanes<C>::NRMAX;
+    const int dl = lane % LD, c = lane / LD;
 #pragma unroll
-        for (int c = 0; c < Tl::CPL; ++c) acc[c] = valid ? xi[c] : 0.0;
-        for (int d = 0; d < ndmax; ++d) {
-            const bool live = valid && d < nd;
-            const double t = live ? Ti[d] : 0.0;
-            const double *x = in + (live ? dpos[d] : 0) * C + cg * Tl::CPL;
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) acc[c] = fma(t, x[c], acc[c]);
-        }
-        if (valid) {
-            double *dst = uout + (size_t)((s ? it.u_off[1] : it.u_off[0]) + i) * C + cg * Tl::CPL;
-#pragma unroll
-            for (int c = 0; c < Tl::CPL; ++c) dst[c] = acc[c];
+    for (int s = 0; s < 2; ++s) {
+        const int k = it.k[s];
+        for (int q0 = 0; q0 < k; q0 += LD * NRMAX) {
+            const int nr = min(NRMAX, (k - q0 + LD - 1) / LD);
+            adj_rows_dispatch<NB, NRMAX>(nr, it, s, ints, dbl, in, q0, dl, c, uout);
         }
     }
 }
 
-// a rows of one (chain, row interval): a_j = sum over its residual blocks of
-// R[j, :] u  (lane = row; every row of the interval is written, zero when no
-// block reaches it)
+// NR rows per lane of one (chain, row interval) group, rows j0 + dl + r LD
+// (r < NR), component c: a_j = sum over the group's residual blocks of
+// R[j, :] x, x the block's u (or g at depth 0)
+template <int NB, int NR>
+__device__ __forceinline__ void adj_r_rows(const BfRGroup &gr, const BfRItem *__restrict__ ritems,
+                                           const int *__restrict__ ints, const double *__restrict__ dbl,
+                                           const double *ubuf, const double *gd, int nmaps, int b0, int j0,
+                                           int dl, int c, double *ad, long long aoff)
+{
+    constexpr int C = 2 * NB, LD = shtb_dev::Lanes<C>::LD;
+    double acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+    const int jend = min(gr.r1, j0 + NR * LD);
+    for (int q = 0; q < gr.nblk; ++q) {
+        const BfRItem it = ritems[ints[gr.blk_off + q]];
+        if (it.j0 >= jend || it.j0 + it.nrows <= j0) continue;       // no row of this pass
+        const double *__restrict__ R = dbl + it.data_off;
+        for (int s = 0; s < it.k; ++s) {
+            const double x = it.to_rings ? __ldg(gd + ((size_t)ints[it.out_off + s] * nmaps + b0) * 2 + c)
+                                         : __ldg(ubuf + (size_t)(it.out_off + s) * C + c);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int j = j0 + dl + r * LD;
+                const bool in_blk = j >= it.j0 && j < it.j0 + it.nrows;
+                const double t = in_blk ? R[(size_t)(j - it.j0) * it.k + s] : 0.0;
+                acc[r] = fma(t, x, acc[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int j = j0 + dl + r * LD;
+        if (j < gr.r1) ad[((size_t)(aoff + 2 * j) * nmaps + b0) * 2 + c] = acc[r];
+    }
+}
+
+template <int NB, int NR>
+__device__ __forceinline__ void adj_r_dispatch(int nr, const BfRGroup &gr, const BfRItem *ritems,
+                                               const int *ints, const double *dbl, const double *ubuf,
+                                               const double *gd, int nmaps, int b0, int j0, int dl, int c,
+                                               double *ad, long long aoff)
+{
+    if constexpr (NR > 1) {
+        if (nr < NR) {
+            adj_r_dispatch<NB, NR - 1>(nr, gr, ritems, ints, dbl, ubuf, gd, nmaps, b0, j0, dl, c, ad, aoff);
+            return;
+        }
+    }
+    adj_r_rows<NB, NR>(gr, ritems, ints, dbl, ubuf, gd, nmaps, b0, j0, dl, c, ad, aoff);
+}
+
+// a rows of one (chain, row interval): every row of the interval is written
+// (zero when no block reaches it), so each chain row has exactly one writer
 template <int NB>
 __global__ void __launch_bounds__(32 * kBfWarps)
 bf_adj_r_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
@@ -230,41 +312,18 @@ bf_adj_r_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
                 const double *__restrict__ u1, const int *__restrict__ depth_par,
                 const double2 *__restrict__ g, int nmaps, int b0, double2 *__restrict__ aacc)
 {
-    constexpr int C = 2 * NB;
+    constexpr int C = 2 * NB, LD = shtb_dev::Lanes<C>::LD, NRMAX = shtb_dev::Lanes<C>::NRMAX;
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * kBfWarps + (threadIdx.x >> 5);
     if (w >= ngroups) return;
     const BfRGroup gr = groups[w];
     const double *ubuf = depth_par[gr.m * 2 + gr.t] ? u1 : u0;
     const long long aoff = shtb_dev::alm_off(v.lmax, gr.m) + gr.t;
-    for (int j = gr.r0 + lane; j < gr.r1; j += 32) {
-        double acc[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = 0.0;
-        for (int q = 0; q < gr.nblk; ++q) {
-            const BfRItem it = ritems[ints[gr.blk_off + q]];
-            if (j < it.j0 || j >= it.j0 + it.nrows) continue;
-            const double *Rj = dbl + it.data_off + (size_t)(j - it.j0) * it.k;
-            for (int s = 0; s < it.k; ++s) {
-                const double r = Rj[s];
-                if (it.to_rings) {
-                    const double2 *x = g + (size_t)ints[it.out_off + s] * nmaps + b0;
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const double2 xb = __ldg(x + b);
-                        acc[2 * b] = fma(r, xb.x, acc[2 * b]);
-                        acc[2 * b + 1] = fma(r, xb.y, acc[2 * b + 1]);
-                    }
-                } else {
-                    const double *x = ubuf + (size_t)(it.out_off + s) * C;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) acc[c] = fma(r, __ldg(x + c), acc[c]);
-                }
-            }
-        }
-        double2 *dst = aacc + (size_t)(aoff + 2 * j) * nmaps + b0;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) dst[b] = make_double2(acc[2 * b], acc[2 * b + 1]);
+    const int dl = lane % LD, c = lane / LD;
+    for (int j0 = gr.r0; j0 < gr.r1; j0 += LD * NRMAX) {
+        const int nr = min(NRMAX, (gr.r1 - j0 + LD - 1) / LD);
+        adj_r_dispatch<NB, NRMAX>(nr, gr, ritems, ints, dbl, ubuf, reinterpret_cast<const double *>(g), nmaps,
+                                  b0, j0, dl, c, reinterpret_cast<double *>(aacc), aoff);
     }
 }
 

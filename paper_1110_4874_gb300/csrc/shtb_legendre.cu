@@ -168,19 +168,37 @@ legendre_synth_kernel(PlanView v, const double2 *__restrict__ ap, double2 *__res
 // g[((m*2 + t)*Z + r)*nmaps + b]: parity combination of the ring-stage
 // adjoint output, g^0 = F(+z_r) + F(-z_r), g^1 = F(+z_r) - F(-z_r); the
 // equator ring (r = Z-1) has no mirror and contributes once.
-__global__ void adjoint_parity_kernel(PlanView v, const double2 *__restrict__ qa,
-                                      double2 *__restrict__ g, int nmaps)
+// One CTA per (half-ring r, run of 64 orders m): reads each map's run of q_adj
+// on ring r and its mirror, and writes the maps of one (m, t, r) entry of g
+// next to each other, up to 16 maps at a time.  Shared memory turns the
+// map-major reads into the entry-major writes, so both are coalesced.
+constexpr int kParityM = 64, kParityMaps = 16;
+
+__global__ void __launch_bounds__(256) adjoint_parity_kernel(PlanView v, const double2 *__restrict__ qa,
+                                                             double2 *__restrict__ g, int nmaps)
 {
-    const int r = blockIdx.x, b = blockIdx.y;
+    __shared__ double2 tile[2][kParityMaps][kParityM];     // north, south
+    const int r = blockIdx.x, m0 = blockIdx.y * kParityM;
     const int Z = v.nhalf, L = v.lmax;
-    const double2 *north = qa + ((size_t)b * v.nrings + r) * (L + 1);
-    const double2 *south = qa + ((size_t)b * v.nrings + (v.nrings - 1 - r)) * (L + 1);
+    const int nm = min(kParityM, L + 1 - m0);
     const bool equator = r == Z - 1;
-    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-        const double2 a = north[m];
-        const double2 c = equator ? make_double2(0.0, 0.0) : south[m];
-        g[(((size_t)m * 2 + 0) * Z + r) * nmaps + b] = make_double2(a.x + c.x, a.y + c.y);
-        g[(((size_t)m * 2 + 1) * Z + r) * nmaps + b] = make_double2(a.x - c.x, a.y - c.y);
+    for (int b0 = 0; b0 < nmaps; b0 += kParityMaps) {
+        const int nb = min(kParityMaps, nmaps - b0);
+        for (int i = threadIdx.x; i < nb * nm; i += blockDim.x) {
+            const int b = i / nm, ml = i - b * nm;
+            const size_t row = (size_t)(b0 + b) * v.nrings;
+            tile[0][b][ml] = qa[(row + r) * (L + 1) + m0 + ml];
+            tile[1][b][ml] = equator ? make_double2(0.0, 0.0) : qa[(row + (v.nrings - 1 - r)) * (L + 1) + m0 + ml];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * nm; i += blockDim.x) {
+            const int ml = i / nb, b = i - ml * nb;
+            const double2 a = tile[0][b][ml], c = tile[1][b][ml];
+            const size_t m = (size_t)(m0 + ml);
+            g[((m * 2 + 0) * Z + r) * nmaps + b0 + b] = make_double2(a.x + c.x, a.y + c.y);
+            g[((m * 2 + 1) * Z + r) * nmaps + b0 + b] = make_double2(a.x - c.x, a.y - c.y);
+        }
+        __syncthreads();
     }
 }
 
@@ -406,7 +424,8 @@ size_t legendre_adjoint_state_bytes(const shtb_plan_s *p)
 int launch_adjoint_parity(const shtb_plan_s *p, const double2 *qadj, double2 *g, int nmaps,
                           cudaStream_t st)
 {
-    adjoint_parity_kernel<<<dim3(p->nhalf, nmaps), 256, 0, st>>>(p->view, qadj, g, nmaps);
+    adjoint_parity_kernel<<<dim3(p->nhalf, (p->lmax + kParityM) / kParityM), 256, 0, st>>>(p->view, qadj, g,
+                                                                                           nmaps);
     ++p->launches;
     SHTB_CUDA_TRY(cudaGetLastError());
     return SHTB_OK;
