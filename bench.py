@@ -195,7 +195,7 @@ def run_ours(args, rank, world, dist):
     t0 = time.perf_counter()
     eps_plan = args.eps
     try:
-        plan = sh.Plan(N, L, eps_plan)
+        plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols)
     except sh.ShtbError as e:
         if e.code != sh.SHTB_ENOTSUP or eps_plan <= 0:
             raise
@@ -320,7 +320,7 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic (seeded Gaussian a_lm, C_l = 1/(l+1)^2)",
         "config": {"workload": f"HEALPix synthesis Nside={N} L={L} batch of {B} maps",
                    "nside": N, "lmax": L, "nmaps": B, "eps_requested": args.eps,
-                   "eps_plan": eps_plan, "compressed": bool(st["compressed"]),
+                   "eps_plan": eps_plan, "compressed": bool(st["compressed"]), "leaf_cols": args.leaf_cols,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (1.07 GB a_lm, 3.2 GB maps per 8 maps)"},
         "roofline": roofline, "hbm": hbm, "e2e": e2e, "gpu_launches": int(launches),
@@ -486,6 +486,7 @@ def main():
     ap.add_argument("--lmax", type=int, default=4096)
     ap.add_argument("--nmaps", type=int, default=8)
     ap.add_argument("--eps", type=float, default=1e-10)
+    ap.add_argument("--leaf-cols", type=int, default=32, help="rings per butterfly leaf block")
     ap.add_argument("--cpu-rings", type=int, default=64, help="ring sample of the CPU baseline")
     ap.add_argument("--ref-rings", type=int, default=16, help="ring sample per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
