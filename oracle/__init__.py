@@ -23,6 +23,8 @@ compression" (arXiv 1110.4874) that it follows:
   real-linear synthesis map under the plain real inner products (the Y^T of
   Eq. (datamodel)/(wiener)): (Y^T f)_l0 = sum_p f_p P_l^0(z_p) and
   (Y^T f)_lm = 2 sum_p f_p P_l^m(z_p) e^{-i m phi_p} for m >= 1.
+* ``analyze`` -- spherical-harmonic analysis by the ring quadrature of Eq.
+  (sh-forward-quadrature), optionally refined by Jacobi steps.
 
 Parity of every function here is pinned by ``tests/test_oracle_pins.py``.
 """
@@ -284,3 +286,34 @@ def gauss_legendre_rings(nrings: int, nphi: int) -> tuple[Rings, np.ndarray]:
     z = x[::-1].copy()
     w = w[::-1].copy()
     return Rings(z, None, np.full(nrings, nphi, np.int32), np.zeros(nrings, np.int32)), w
+
+
+def _m_of_index(lmax: int) -> np.ndarray:
+    """m of every stored coefficient (m-major layout, l = m..lmax)."""
+    return np.repeat(np.arange(lmax + 1), np.arange(lmax + 1, 0, -1))
+
+
+def analyze(rings: Rings, lmax: int, maps, ring_weight, niter: int = 0,
+            nthreads: int = 0) -> np.ndarray:
+    """Spherical-harmonic analysis by the quadrature rule of Eq.
+    (sh-forward-quadrature): a_lm = sum_p w_p f_p conj(Y_lm(p)), with w_p
+    the weight of pixel p's ring (``ring_weight[k]``, one per ring).
+
+    conj(Y_lm(p)) = Ptilde_l^m(z_p) e^{-i m phi_p}, so the sum is the
+    real-inner-product adjoint of ``adjoint`` applied to the weighted map,
+    halved for m >= 1 (that adjoint carries the factor 2 of the -m terms).
+    With ``niter`` > 0 the estimate is refined by Jacobi steps
+    a <- a + A (f - Y a), A the quadrature rule above: the quadrature is
+    not exact on HEALPix (Sec. 2.3), and each step removes part of the
+    error.  Complex [nmaps, nalm]."""
+    f = np.atleast_2d(np.asarray(maps, dtype=np.float64))
+    w = np.repeat(np.asarray(ring_weight, dtype=np.float64), rings.J)
+    h = np.where(_m_of_index(lmax) == 0, 1.0, 0.5)
+
+    def quad(g):
+        return adjoint(rings, lmax, g * w, nthreads) * h
+
+    a = quad(f)
+    for _ in range(niter):
+        a = a + quad(f - synthesize(rings, lmax, a, nthreads))
+    return a

@@ -311,6 +311,51 @@ def test_gauss_legendre_discrete_analysis_roundtrip():
     np.testing.assert_allclose(back, want, atol=2e-13)
 
 
+def test_analysis_exact_on_gauss_legendre_grid():
+    """oracle.analyze with the Gauss-Legendre weights (2 pi w_k / J per pixel)
+    recovers a band-limited a_lm exactly: the quadrature of Eq.
+    (sh-forward-quadrature) is exact there for l, l' <= L (L+1 rings,
+    J >= 2L+1).  A wrong weight, a missing 1/2 for m >= 1 or a flipped phase
+    sign each fail this."""
+    lmax = 12
+    rings, w = oracle.gauss_legendre_rings(lmax + 1, 2 * lmax + 1)
+    a = _random_alm(lmax, 2, 31)
+    f = oracle.synthesize(rings, lmax, a)
+    back = oracle.analyze(rings, lmax, f, 2 * math.pi * w / rings.J)
+    np.testing.assert_allclose(back, a, atol=5e-14)
+
+
+def test_analysis_of_constant_map_on_healpix():
+    """f = 1 on the HEALPix grid with the equal-area weight 4 pi / npix:
+    a_00 = sqrt(4 pi) exactly (the weights sum to 4 pi and P_0^0 =
+    1/sqrt(4 pi)), and every m = 1, 2, 3 coefficient vanishes because each
+    ring's longitude sum of e^{-i m phi} is zero for 0 < m < J (J >= 4)."""
+    nside, lmax = 8, 16
+    rings = oracle.healpix_rings(nside)
+    w = np.full(rings.nrings, 4 * math.pi / rings.npix)
+    a = oracle.analyze(rings, lmax, np.ones((1, rings.npix)), w)[0]
+    assert a[0] == pytest.approx(math.sqrt(4 * math.pi), rel=1e-14)
+    mcol = np.array([m for m in range(lmax + 1) for _ in range(m, lmax + 1)])
+    assert np.abs(a[(mcol >= 1) & (mcol <= 3)]).max() < 1e-15
+
+
+def test_analysis_jacobi_refinement_converges_on_healpix():
+    """The HEALPix quadrature is not exact, but for L <= 2 nside each Jacobi
+    step a <- a + A (f - Y a) shrinks the error of a band-limited round trip
+    by a roughly constant factor; after 16 steps it is at rounding level."""
+    nside = 8
+    rings = oracle.healpix_rings(nside)
+    w = np.full(rings.nrings, 4 * math.pi / rings.npix)
+    for lmax in (8, 16):
+        a = _random_alm(lmax, 1, 40 + lmax)
+        f = oracle.synthesize(rings, lmax, a)
+        err = [np.abs(oracle.analyze(rings, lmax, f, w, niter=k) - a).max() / np.abs(a).max()
+               for k in (0, 1, 2, 4, 8, 16)]
+        assert err[0] > 1e-3                        # plain quadrature: visibly inexact
+        assert all(e1 < 0.2 * e0 for e0, e1 in zip(err[:-1], err[1:]) if e0 > 1e-13)
+        assert err[-1] < 1e-14
+
+
 def test_adjoint_dot_product_identity():
     """<Y a, f> = <a, Y^T f> with real inner products over (Re, Im) a_lm."""
     nside, lmax = 8, 16
