@@ -58,14 +58,14 @@ NCU_TRAFFIC = {
     "bf_level_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.h"],
-        "sha256": "d107543be69049449cd86cea14dabbd53c10e1448ae0840a079ac7e46460faf5",
-        "bytes": 61_850_000_000 + 24_940_000_000,     # read + write over the 6 level launches
+        "sha256": "a9b91890587d5c09b2a5a775cb2f179d8a821748ed05a3c9fc54fe5980b8eba4",
+        "bytes": 61_900_000_000 + 24_990_000_000,     # read + write over the 6 level launches
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
     "bf_r_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.h"],
-        "sha256": "d107543be69049449cd86cea14dabbd53c10e1448ae0840a079ac7e46460faf5",
+        "sha256": "a9b91890587d5c09b2a5a775cb2f179d8a821748ed05a3c9fc54fe5980b8eba4",
         "bytes": 10_720_000_000 + 3_640_000_000,
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
@@ -255,6 +255,14 @@ def run_ours(args, rank, world, dist):
     adj()
     ms_adj = timed(adj, args.steps) / (args.steps * B * world)
 
+    # ---- analysis (quadrature + Jacobi refinement) of the same batch
+    analysis = None
+    if not args.no_patterns:
+        analysis = {"maps": B}
+        for k in (0, 3):
+            ana = lambda: plan.analyze(f, niter=k, out=aout)  # noqa: E731
+            analysis[f"niter{k}_ms_per_map"] = round(event_ms(ana, 1) / B, 3)
+
     # ---- plain: one map per launch
     def plain():
         for b in range(B):
@@ -338,6 +346,8 @@ def run_ours(args, rank, world, dist):
     plan.close()
     del alm, maps, f, aout
     torch.cuda.empty_cache()
+    if analysis is not None:
+        out["details"]["analysis"] = analysis
     if rank == 0 and not args.no_patterns:
         out["details"]["batched_serving"], plan_c4 = batched_serving(sh, synthetic, dev)
         out["details"]["differentiation"] = differentiation(sh, synthetic, dev, plan_c4)

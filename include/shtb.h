@@ -71,6 +71,10 @@ typedef struct {
                           compressing; <= 0 = library default                         */
     int nthreads;      /* host threads used while building the plan; 0 = all cores   */
     int device;        /* CUDA device ordinal; -1 = the calling thread's current one  */
+    const char *cache_dir; /* NULL, or a directory of plan files: shtb_plan_create loads
+                          the plan of this (nside, lmax, eps, options) from it if a
+                          valid file is there, else builds the plan and writes the
+                          file (a missing, unreadable or corrupt file is rebuilt)   */
 } shtb_plan_opts;
 
 /* Plan statistics (algorithmic counts; used for roofline accounting). */
@@ -97,6 +101,7 @@ typedef struct {
     long long kernel_launches;      /* CUDA kernels this plan has launched so far     */
     long long n_ident;              /* identity entries of the interpolation matrices  */
     int depth_hist[16];             /* (m, parity) count per butterfly depth          */
+    int from_cache;                 /* 1: the plan was read from a plan file          */
 } shtb_plan_stats_t;
 
 /* Fill *opts with defaults.  Returns SHTB_EINVAL on NULL. */
@@ -124,6 +129,19 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
 
 /* Release a plan and all device memory it owns (NULL is accepted). */
 int shtb_plan_destroy(shtb_plan plan);
+
+/*
+ * Plan files (the paper's precomputed-data files).  shtb_plan_save writes
+ * the plan -- host tables and every device array, with a format version, the
+ * plan's key (nside, lmax, eps, leaf_cols, max_depth, rho) and a checksum --
+ * to `path` (written to path.tmp, then renamed).  shtb_plan_load builds a
+ * plan on opts->device (or the current device; other opts fields are taken
+ * from the file) from such a file.  Errors: SHTB_EIO (cannot open, read or
+ * write), SHTB_ECORRUPT (wrong magic, version or key, truncated, checksum
+ * mismatch), SHTB_EINVAL, SHTB_ENOMEM, SHTB_ECUDA.
+ */
+int shtb_plan_save(shtb_plan plan, const char *path);
+int shtb_plan_load(const char *path, const shtb_plan_opts *opts, shtb_plan *out);
 
 /* Copy the plan's statistics into *out. */
 int shtb_plan_stats(shtb_plan plan, shtb_plan_stats_t *out);
@@ -157,6 +175,25 @@ int shtb_synthesize(shtb_plan plan, const double *alm_dev, double *map_dev, int 
  */
 int shtb_adjoint(shtb_plan plan, const double *map_dev, double *alm_dev, int nmaps,
                  void *stream);
+
+/*
+ * Spherical-harmonic analysis by ring quadrature (Eq. sh-forward-quadrature):
+ * a_lm = sum_p w_p f_p conj(Y_lm(p)), w_p = ring_weight_dev[ring of p], then
+ * niter Jacobi refinement steps a <- a + A (f - Y a), A the quadrature rule
+ * (the HEALPix quadrature is not exact, Sec. 2.3; each step costs one
+ * synthesis and one adjoint and shrinks the error of a band-limited map by
+ * a roughly constant factor for lmax <= 2 nside).
+ * map_dev: [nmaps][12 nside^2] float64 (read only); alm_dev: [nmaps][nalm]
+ * complex128 (written; Im a_l0 = 0).  ring_weight_dev: device, one double
+ * per ring (4 nside - 1), the weight of every pixel of that ring; NULL means
+ * the equal-area HEALPix weight 4 pi / (12 nside^2).  The plan's workspace
+ * holds the residual map, so calls on one plan are stream-ordered.
+ * Errors as shtb_synthesize; SHTB_EINVAL also for niter outside
+ * 0..SHTB_MAX_ANALYSIS_ITER or map_dev == alm_dev.
+ */
+#define SHTB_MAX_ANALYSIS_ITER 64
+int shtb_analyze(shtb_plan plan, const double *map_dev, double *alm_dev, int nmaps,
+                 const double *ring_weight_dev, int niter, void *stream);
 
 /*
  * The same two transforms between HOST buffers: the call copies the inputs

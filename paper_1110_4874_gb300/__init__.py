@@ -43,7 +43,8 @@ class ShtbError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("leaf_cols", ctypes.c_int), ("max_depth", ctypes.c_int),
-                ("rho", ctypes.c_double), ("nthreads", ctypes.c_int), ("device", ctypes.c_int)]
+                ("rho", ctypes.c_double), ("nthreads", ctypes.c_int), ("device", ctypes.c_int),
+                ("cache_dir", ctypes.c_char_p)]
 
 
 class PlanStats(ctypes.Structure):
@@ -55,7 +56,8 @@ class PlanStats(ctypes.Structure):
                 ("plan_read_bytes", ctypes.c_longlong), ("legendre_flops_per_map", ctypes.c_double),
                 ("recurrence_flops", ctypes.c_double), ("phi_flops_per_map", ctypes.c_double),
                 ("build_seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
-                ("n_ident", ctypes.c_longlong), ("depth_hist", ctypes.c_int * 16)]
+                ("n_ident", ctypes.c_longlong), ("depth_hist", ctypes.c_int * 16),
+                ("from_cache", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "depth_hist"}
@@ -85,10 +87,13 @@ SIGNATURES = {
     "shtb_plan_opts_init": (_I, [ctypes.POINTER(PlanOpts)]),
     "shtb_plan_create": (_I, [_I, _I, _D, ctypes.POINTER(PlanOpts), ctypes.POINTER(_P)]),
     "shtb_plan_destroy": (_I, [_P]),
+    "shtb_plan_save": (_I, [_P, ctypes.c_char_p]),
+    "shtb_plan_load": (_I, [ctypes.c_char_p, ctypes.POINTER(PlanOpts), ctypes.POINTER(_P)]),
     "shtb_plan_stats": (_I, [_P, ctypes.POINTER(PlanStats)]),
     "shtb_plan_reserve": (_I, [_P, _I]),
     "shtb_synthesize": (_I, [_P, _P, _P, _I, _P]),
     "shtb_adjoint": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_analyze": (_I, [_P, _P, _P, _I, _P, _I, _P]),
     "shtb_synthesize_host": (_I, [_P, _P, _P, _I, _P]),
     "shtb_adjoint_host": (_I, [_P, _P, _P, _I, _P]),
     "shtb_strerror": (ctypes.c_char_p, [_I]),
@@ -187,10 +192,11 @@ def shtb_last_error_message() -> str:
 
 def shtb_plan_create(nside: int, lmax: int, eps: float = 0.0, leaf_cols: int = 32,
                      max_depth: int = -1, rho: float = 0.0, nthreads: int = 0,
-                     device: int = -1) -> ctypes.c_void_p:
+                     device: int = -1, cache_dir: str | None = None) -> ctypes.c_void_p:
     opts = shtb_plan_opts_init()
     opts.leaf_cols, opts.max_depth, opts.rho = leaf_cols, max_depth, rho
     opts.nthreads, opts.device = nthreads, device
+    opts.cache_dir = os.fsencode(cache_dir) if cache_dir is not None else None
     h = ctypes.c_void_p()
     _check(lib().shtb_plan_create(nside, lmax, float(eps), ctypes.byref(opts), ctypes.byref(h)),
            "shtb_plan_create")
@@ -199,6 +205,18 @@ def shtb_plan_create(nside: int, lmax: int, eps: float = 0.0, leaf_cols: int = 3
 
 def shtb_plan_destroy(plan) -> None:
     _check(lib().shtb_plan_destroy(plan), "shtb_plan_destroy")
+
+
+def shtb_plan_save(plan, path: str) -> None:
+    _check(lib().shtb_plan_save(plan, os.fsencode(path)), "shtb_plan_save")
+
+
+def shtb_plan_load(path: str, device: int = -1) -> ctypes.c_void_p:
+    opts = shtb_plan_opts_init()
+    opts.device = device
+    h = ctypes.c_void_p()
+    _check(lib().shtb_plan_load(os.fsencode(path), ctypes.byref(opts), ctypes.byref(h)), "shtb_plan_load")
+    return h
 
 
 def shtb_plan_stats(plan) -> dict:
@@ -234,6 +252,17 @@ def shtb_synthesize_noalloc(plan, alm, maps, nmaps: int, stream=None) -> None:
 def shtb_adjoint(plan, maps, alm, nmaps: int, stream=None) -> None:
     import torch
     _call_dev("shtb_adjoint", plan, maps, torch.float64, alm, torch.complex128, nmaps, stream)
+
+
+def shtb_analyze(plan, maps, alm, nmaps: int, ring_weight=None, niter: int = 0,
+                 stream=None) -> None:
+    """Quadrature analysis (+ niter Jacobi steps); ring_weight: None (equal
+    area 4 pi / npix) or a contiguous float64 device tensor, one per ring."""
+    import torch
+    w = None if ring_weight is None else _dptr(ring_weight, torch.float64, "ring_weight")
+    _check(lib().shtb_analyze(plan, _dptr(maps, torch.float64, "maps"),
+                              _dptr(alm, torch.complex128, "alm"), int(nmaps), w, int(niter),
+                              _stream_handle(stream)), "shtb_analyze")
 
 
 def _hptr(t, dtype, name):
@@ -451,6 +480,36 @@ class Plan:
             out = torch.empty((nmaps, self.nalm), dtype=torch.complex128, device=f.device)
         shtb_adjoint(self._h, f, out, nmaps, stream)
         return out[0] if squeeze else out
+
+    def analyze(self, maps, niter: int = 0, ring_weight=None, out=None, stream=None):
+        """maps float64 [nmaps, npix] (or [npix]) -> a_lm complex128 by ring
+        quadrature plus ``niter`` Jacobi refinement steps (shtb_analyze)."""
+        import torch
+        squeeze = maps.dim() == 1
+        f = maps.reshape(-1, self.npix).contiguous()
+        nmaps = f.shape[0]
+        if ring_weight is not None and ring_weight.numel() != self.nrings:
+            raise ValueError(f"ring_weight needs one weight per ring ({self.nrings})")
+        if out is None:
+            out = torch.empty((nmaps, self.nalm), dtype=torch.complex128, device=f.device)
+        shtb_analyze(self._h, f, out, nmaps, ring_weight, niter, stream)
+        return out[0] if squeeze else out
+
+    def save(self, path: str) -> None:
+        """Write the plan to a plan file (shtb_plan_save)."""
+        shtb_plan_save(self._h, path)
+
+    @classmethod
+    def load(cls, path: str, device: int | None = None) -> "Plan":
+        """A plan read from a plan file (shtb_plan_load) on `device`."""
+        import torch
+        self = cls.__new__(cls)
+        self.device = torch.cuda.current_device() if device is None else device
+        self._h = shtb_plan_load(path, self.device)
+        st = shtb_plan_stats(self._h)
+        self.nside, self.lmax, self.eps = st["nside"], st["lmax"], st["eps"]
+        self.npix, self.nalm, self.nrings = st["npix"], st["nalm"], st["nrings"]
+        return self
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

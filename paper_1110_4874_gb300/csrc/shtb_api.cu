@@ -222,6 +222,7 @@ int shtb_plan_opts_init(shtb_plan_opts *o)
     o->rho = 0.0;
     o->nthreads = 0;
     o->device = -1;
+    o->cache_dir = nullptr;
     return SHTB_OK;
 }
 
@@ -255,12 +256,40 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
         return shtb_fail(SHTB_ECUDA, "cudaSetDevice failed");
     }
     p->device = dev;
-    int rc = shtb_build_dense_plan(p);
-    if (rc == SHTB_OK && eps > 0.0) rc = shtb_build_butterfly(p);
-    if (rc) {
-        shtb_plan_destroy(p);
-        return rc;
+    int rc = SHTB_OK;
+    bool loaded = false;
+    std::string cpath;
+    if (o.cache_dir) {
+        cpath = plan_cache_path(p, o.cache_dir);
+        if (plan_load(p, cpath.c_str()) == SHTB_OK) {
+            loaded = true;
+        } else {                          // missing or invalid file: start over and rebuild
+            shtb_plan_s *fresh = new (std::nothrow) shtb_plan_s();
+            if (!fresh) {
+                shtb_plan_destroy(p);
+                return shtb_fail(SHTB_ENOMEM, "plan struct");
+            }
+            fresh->opts = p->opts;
+            fresh->nside = nside;
+            fresh->lmax = lmax;
+            fresh->eps = eps;
+            fresh->device = dev;
+            shtb_plan_destroy(p);
+            p = fresh;
+        }
     }
+    if (!loaded) {
+        rc = shtb_build_dense_plan(p);
+        if (rc == SHTB_OK && eps > 0.0) rc = shtb_build_butterfly(p);
+        if (rc) {
+            shtb_plan_destroy(p);
+            return rc;
+        }
+        if (o.cache_dir) plan_save(p, cpath.c_str());   // a cache that cannot be written is only slower
+    }
+    p->opts.cache_dir = nullptr;          // the caller's string is not kept
+    p->stats.from_cache = loaded ? 1 : 0;
+    p->stats.kernel_launches = 0;
     p->stats.nside = nside;
     p->stats.lmax = lmax;
     p->stats.eps = eps;
@@ -273,6 +302,55 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
     }
     p->stats.build_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SHTB_OK;
+}
+
+int shtb_plan_save(shtb_plan p, const char *path)
+{
+    if (!p || !path) return shtb_fail(SHTB_EINVAL, "plan or path is NULL");
+    int prev = -1;
+    SHTB_CUDA_TRY(cudaGetDevice(&prev));
+    if (prev != p->device) SHTB_CUDA_TRY(cudaSetDevice(p->device));
+    const int rc = plan_save(p, path);
+    if (prev != p->device) cudaSetDevice(prev);
+    return rc;
+}
+
+int shtb_plan_load(const char *path, const shtb_plan_opts *opts, shtb_plan *out)
+{
+    if (!out || !path) return shtb_fail(SHTB_EINVAL, "out or path is NULL");
+    *out = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    shtb_plan_opts o;
+    shtb_plan_opts_init(&o);
+    if (opts) o.device = opts->device;
+    int nside = 0, lmax = 0;
+    double eps = 0.0;
+    int rc = plan_read_key(path, &nside, &lmax, &eps, &o);
+    if (rc) return rc;
+    int dev = o.device;
+    if (dev < 0) {
+        SHTB_CUDA_TRY(cudaGetDevice(&dev));
+    } else {
+        SHTB_CUDA_TRY(cudaSetDevice(dev));
+    }
+    shtb_plan_s *p = new (std::nothrow) shtb_plan_s();
+    if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
+    o.device = dev;
+    o.cache_dir = nullptr;
+    p->opts = o;
+    p->nside = nside;
+    p->lmax = lmax;
+    p->eps = eps;
+    p->device = dev;
+    if ((rc = plan_load(p, path))) {
+        shtb_plan_destroy(p);
+        return rc;
+    }
+    p->stats.from_cache = 1;
+    p->stats.kernel_launches = 0;
+    p->stats.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
     return SHTB_OK;
 }
@@ -323,6 +401,34 @@ int shtb_adjoint(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps,
     int rc = check_call(p, map_dev, alm_dev, nmaps);
     if (rc) return rc;
     return run_adjoint(p, map_dev, (double2 *)alm_dev, nmaps, (cudaStream_t)stream);
+}
+
+int shtb_analyze(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps,
+                 const double *ring_weight_dev, int niter, void *stream)
+{
+    int rc = check_call(p, map_dev, alm_dev, nmaps);
+    if (rc) return rc;
+    if (niter < 0 || niter > SHTB_MAX_ANALYSIS_ITER)
+        return shtb_fail(SHTB_EINVAL, "niter must be in 0.." + std::to_string(SHTB_MAX_ANALYSIS_ITER));
+    if ((const void *)map_dev == (const void *)alm_dev)
+        return shtb_fail(SHTB_EINVAL, "map and alm must not alias");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_ws(p, nmaps))) return rc;
+    Workspace w = carve(p, nmaps);   // w.map: weighted residual, w.alm: adjoint of it
+    double2 *alm = (double2 *)alm_dev;
+    const double w0 = 4.0 * 3.14159265358979323846 / (double)p->npix;   // equal-area HEALPix pixel weight
+    // a = A f
+    if ((rc = launch_ring_weight(p, map_dev, nullptr, ring_weight_dev, w0, w.map, nmaps, st))) return rc;
+    if ((rc = run_adjoint(p, w.map, alm, nmaps, st))) return rc;
+    if ((rc = launch_alm_quadrature_add(p, alm, alm, nmaps, true, st))) return rc;
+    // Jacobi refinement: a += A (f - Y a)
+    for (int it = 0; it < niter; ++it) {
+        if ((rc = run_synthesis(p, alm, w.map, nmaps, st))) return rc;
+        if ((rc = launch_ring_weight(p, map_dev, w.map, ring_weight_dev, w0, w.map, nmaps, st))) return rc;
+        if ((rc = run_adjoint(p, w.map, w.alm, nmaps, st))) return rc;
+        if ((rc = launch_alm_quadrature_add(p, w.alm, alm, nmaps, false, st))) return rc;
+    }
+    return SHTB_OK;
 }
 
 int shtb_synthesize_host(shtb_plan p, const double *alm_host, double *map_host, int nmaps,

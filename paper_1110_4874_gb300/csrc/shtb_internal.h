@@ -130,8 +130,9 @@ struct shtb_plan_s {
     // power-of-two Bluestein length)
     int max_K_pow2 = 0, max_M_blue = 0;
 
-    // device allocations owned by the plan (freed in destroy)
+    // device allocations owned by the plan (freed in destroy), with their sizes
     std::vector<void *> allocations;
+    std::vector<size_t> alloc_bytes;
     PlanView view{};
 
     // butterfly-compressed operator (eps > 0), owned
@@ -167,6 +168,14 @@ int shtb_build_dense_plan(shtb_plan_s *p);
 // Device allocation helper that registers the pointer with the plan.
 int plan_alloc_upload(shtb_plan_s *p, void **dst, const void *src, size_t bytes);
 
+// Plan cache files (shtb_plan_cache.cpp): write a built plan; fill a fresh
+// plan whose key (nside, lmax, eps, opts) and device are set; the file name
+// of a plan in a cache directory.
+int plan_save(shtb_plan_s *p, const char *path);
+int plan_load(shtb_plan_s *p, const char *path);
+std::string plan_cache_path(const shtb_plan_s *p, const char *dir);
+int plan_read_key(const char *path, int *nside, int *lmax, double *eps, shtb_plan_opts *opts);
+
 // ---------------------------------------------------------- kernel launches
 // shtb_legendre.cu
 int launch_alm_prescale(const shtb_plan_s *p, const double2 *alm, double2 *aprime, int nmaps,
@@ -196,6 +205,13 @@ int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, doub
                             int b0, cudaStream_t st);
 
 // shtb_butterfly.cu
+// analysis (shtb_analysis.cu): quadrature weighting of a map or a residual,
+// and alm += h_m g with h_0 = 1, h_m = 1/2
+int launch_ring_weight(const shtb_plan_s *p, const double *f, const double *y, const double *ring_w,
+                       double w0, double *r, int nmaps, cudaStream_t st);
+int launch_alm_quadrature_add(const shtb_plan_s *p, const double2 *g, double2 *alm, int nmaps,
+                              bool first, cudaStream_t st);
+
 size_t bf_workspace_bytes(const shtb_plan_s *p);
 // map != nullptr: the whole synthesis; map == nullptr: the Legendre stage
 // alone, q^t of map b written to qt_out + b [2][nhalf][L+1] complex

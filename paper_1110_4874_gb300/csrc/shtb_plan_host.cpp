@@ -402,6 +402,7 @@ int plan_alloc_upload(shtb_plan_s *p, void **dst, const void *src, size_t bytes)
     if (e != cudaSuccess)
         return shtb_fail(SHTB_ENOMEM, std::string("cudaMalloc plan table: ") + cudaGetErrorString(e));
     p->allocations.push_back(d);
+    p->alloc_bytes.push_back(nb);
     if (src && bytes) {
         e = cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess)
