@@ -180,6 +180,23 @@ def oracle_sample(nside, lmax, nmaps_sample, nrings_sample, seed, nthreads=0):
 
 
 # -------------------------------------------------------------- our arm
+def reduce_max(x, dist, device):
+    """The largest of the ranks' values of x (each rank's own time); x
+    itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def ms_per_map(ms_slowest, steps, nmaps, world):
+    """Whole-job time per map: every rank transforms nmaps maps per step, so
+    the job's maps are steps * nmaps * world in the slowest rank's time."""
+    return ms_slowest / (steps * nmaps * world)
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -226,12 +243,7 @@ def run_ours(args, rank, world, dist):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reduce_max(e0.elapsed_time(e1), dist, dev)
 
     synth = lambda: plan.synthesize(alm, out=maps)  # noqa: E731
     for _ in range(args.warmup):
@@ -246,14 +258,14 @@ def run_ours(args, rank, world, dist):
     stages, ncalls = sh.shtb_profile_read(plan.handle)
     sh.shtb_profile_enable(plan.handle, False)
     clocks = clk.summary()
-    value = ms_total / (args.steps * B * world)
+    value = ms_per_map(ms_total, args.steps, B, world)
 
     # ---- adjoint of the same batch
     f = torch.from_numpy(synthetic.gaussian_map(plan.npix, B, seed=3000 + rank)).to(dev)
     aout = torch.empty((B, plan.nalm), dtype=torch.complex128, device=dev)
     adj = lambda: plan.adjoint(f, out=aout)  # noqa: E731
     adj()
-    ms_adj = timed(adj, args.steps) / (args.steps * B * world)
+    ms_adj = ms_per_map(timed(adj, args.steps), args.steps, B, world)
 
     # ---- analysis (quadrature + Jacobi refinement) of the same batch
     analysis = None
@@ -268,7 +280,7 @@ def run_ours(args, rank, world, dist):
         for b in range(B):
             plan.synthesize(alm[b:b + 1], out=maps[b:b + 1])
     plain()
-    ms_plain = timed(plain, args.steps) / (args.steps * B * world)
+    ms_plain = ms_per_map(timed(plain, args.steps), args.steps, B, world)
 
     # ---- end to end through the C ABI with host buffers (copies inside)
     maps_h = torch.empty((B, plan.npix), dtype=torch.float64).pin_memory()
@@ -277,12 +289,8 @@ def run_ours(args, rank, world, dist):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         sh.shtb_synthesize_host(plan.handle, alm_h, maps_h, B)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": e2e_s * 1e3 / (args.steps * B * world), "unit": UNIT,
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": ms_per_map(e2e_s * 1e3, args.steps, B, world), "unit": UNIT,
            "h2d_bytes_per_step": int(alm_h.numel() * alm_h.element_size()),
            "d2h_bytes_per_step": int(maps_h.numel() * maps_h.element_size())}
 

@@ -111,6 +111,11 @@ struct shtb_plan_s {
     // radix 11 or 13), heaviest rings first
     std::vector<int> direct_rings, blue_rings, big_rings;
     int max_K_direct = 0, max_M_mx = 0, max_K_big = 0;
+    // Bluestein rings blue_rings[blue_split..] have transforms of at most
+    // kBlueSmallM points (the longest max_M_small): they run at half the
+    // threads per CTA, two CTAs per SM
+    static constexpr int kBlueSmallM = 7168;
+    int blue_split = 0, max_M_small = 0;
     int *d_direct_rings = nullptr, *d_blue_rings = nullptr, *d_big_rings = nullptr;
     // the rings cut into kPhiChunks runs of consecutive rings with about equal
     // pixel counts, per run and ring variant a device list (chunk_list + off)
@@ -120,6 +125,7 @@ struct shtb_plan_s {
     static constexpr int kPhiChunks = 4;
     struct ChunkKind {
         int off, n, len;
+        int split, len_small;   // as blue_split / max_M_small, within this list
     };
     ChunkKind chunk_kind[kPhiChunks][3] = {};
     long long chunk_pix[kPhiChunks + 1] = {};

@@ -114,41 +114,64 @@ phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__re
 }
 
 // one launch per ring kind: grid (rings of that kind) x maps, shared memory
-// for the kind's longest transform
+// for the kind's longest transform.  The Bluestein list is cut in two:
+// rings [0, split) at phi_threads (one CTA per SM at the longest lengths),
+// rings [split, n) -- transforms of at most kBlueSmallM points -- at half the
+// threads with shared memory for their own longest transform, so that two
+// CTAs share an SM and one's barriers between FFT passes are covered by the
+// other's work.  Every body loops over blockDim.x.
 struct RingSet {
     const int *rings;
-    size_t n;
-    int len;
+    int n, len;
+    int split, len_small;
 };
 
 RingSet ring_set(const shtb_plan_s *p, int kind)
 {
-    if (kind == kDirect) return {p->d_direct_rings, p->direct_rings.size(), p->max_K_direct};
-    if (kind == kBluestein) return {p->d_blue_rings, p->blue_rings.size(), p->max_M_mx};
-    return {p->d_big_rings, p->big_rings.size(), p->max_K_big};
+    if (kind == kDirect)
+        return {p->d_direct_rings, (int)p->direct_rings.size(), p->max_K_direct, (int)p->direct_rings.size(), 0};
+    if (kind == kBluestein)
+        return {p->d_blue_rings, (int)p->blue_rings.size(), p->max_M_mx, p->blue_split, p->max_M_small};
+    return {p->d_big_rings, (int)p->big_rings.size(), p->max_K_big, (int)p->big_rings.size(), 0};
+}
+
+// launch(rings, n, threads, smem bytes) for each non-empty part of rs
+template <int KIND, class Launch>
+int launch_parts(const shtb_plan_s *p, const RingSet &rs, const void *kernel, Launch launch)
+{
+    if (rs.n == 0) return SHTB_OK;
+    SHTB_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double2) * (size_t)rs.len)));
+    if (rs.split > 0) {
+        launch(rs.rings, rs.split, phi_threads<KIND>(), sizeof(double2) * (size_t)rs.len);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    if (rs.split < rs.n) {
+        launch(rs.rings + rs.split, rs.n - rs.split, phi_threads<KIND>() / 2,
+               sizeof(double2) * (size_t)rs.len_small);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    }
+    return SHTB_OK;
 }
 
 template <int KIND>
 int launch_kind(const shtb_plan_s *p, bool synth, const void *in, void *out, int nmaps, cudaStream_t st)
 {
     const RingSet rs = ring_set(p, KIND);
-    if (rs.n == 0) return SHTB_OK;
-    const size_t smem = sizeof(double2) * (size_t)rs.len;
-    const dim3 grid((unsigned)rs.n, (unsigned)nmaps);
-    if (synth) {
-        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        phi_synth_kernel<KIND><<<grid, phi_threads<KIND>(), smem, st>>>(p->view, rs.rings, (const double2 *)in,
-                                                                (double *)out);
-    } else {
-        SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_adjoint_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        phi_adjoint_kernel<KIND><<<grid, phi_threads<KIND>(), smem, st>>>(p->view, rs.rings, (const double *)in,
-                                                                  (double2 *)out);
-    }
-    SHTB_CUDA_TRY(cudaGetLastError());
-    ++p->launches;
-    return SHTB_OK;
+    const PlanView v = p->view;
+    if (synth)
+        return launch_parts<KIND>(p, rs, (const void *)phi_synth_kernel<KIND>,
+                                  [&](const int *rings, int n, int threads, size_t smem) {
+                                      phi_synth_kernel<KIND><<<dim3((unsigned)n, (unsigned)nmaps), threads, smem,
+                                                               st>>>(v, rings, (const double2 *)in, (double *)out);
+                                  });
+    return launch_parts<KIND>(p, rs, (const void *)phi_adjoint_kernel<KIND>,
+                              [&](const int *rings, int n, int threads, size_t smem) {
+                                  phi_adjoint_kernel<KIND><<<dim3((unsigned)n, (unsigned)nmaps), threads, smem,
+                                                             st>>>(v, rings, (const double *)in, (double2 *)out);
+                              });
 }
 
 int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int nmaps,
@@ -161,33 +184,29 @@ int launch_set(const shtb_plan_s *p, bool synth, const void *in, void *out, int 
 }
 
 template <int KIND>
-int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0, cudaStream_t st)
+int launch_qt_set(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0, const RingSet &rs,
+                  cudaStream_t st)
 {
-    const RingSet rs = ring_set(p, KIND);
-    if (rs.n == 0) return SHTB_OK;
-    const size_t smem = sizeof(double2) * (size_t)rs.len;
-    SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    phi_synth_qt_kernel<KIND><<<dim3((unsigned)rs.n, (unsigned)nb), phi_threads<KIND>(), smem, st>>>(p->view, rs.rings,
-                                                                                            qt, map, b0);
-    SHTB_CUDA_TRY(cudaGetLastError());
-    ++p->launches;
-    return SHTB_OK;
+    const PlanView v = p->view;
+    return launch_parts<KIND>(p, rs, (const void *)phi_synth_qt_kernel<KIND>,
+                              [&](const int *rings, int n, int threads, size_t smem) {
+                                  phi_synth_qt_kernel<KIND><<<dim3((unsigned)n, (unsigned)nb), threads, smem, st>>>(
+                                      v, rings, qt, map, b0);
+                              });
 }
 
 template <int KIND>
-int launch_qt_list(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0, const int *rings,
-                   int n, int len, cudaStream_t st)
+int launch_qt_kind(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0, cudaStream_t st)
 {
-    if (n == 0) return SHTB_OK;
-    const size_t smem = sizeof(double2) * (size_t)len;
-    SHTB_CUDA_TRY(cudaFuncSetAttribute(phi_synth_qt_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    phi_synth_qt_kernel<KIND><<<dim3((unsigned)n, (unsigned)nb), phi_threads<KIND>(), smem, st>>>(p->view, rings,
-                                                                                                 qt, map, b0);
-    SHTB_CUDA_TRY(cudaGetLastError());
-    ++p->launches;
-    return SHTB_OK;
+    return launch_qt_set<KIND>(p, qt, nb, map, b0, ring_set(p, KIND), st);
+}
+
+template <int KIND>
+int launch_qt_list(const shtb_plan_s *p, const double2 *qt, int nb, MapOut map, int b0,
+                   const shtb_plan_s::ChunkKind &ck, cudaStream_t st)
+{
+    return launch_qt_set<KIND>(p, qt, nb, map, b0, RingSet{p->d_chunk_list + ck.off, ck.n, ck.len,
+                                                           KIND == kBluestein ? ck.split : ck.n, ck.len_small}, st);
 }
 
 int launch_qt_all(const shtb_plan_s *p, const double *qt, int nb, MapOut mo, int b0, cudaStream_t st)
@@ -214,11 +233,9 @@ int launch_phi_synth_qt_chunk(const shtb_plan_s *p, const double *qt, int nb, do
     const MapOut mo{map, nullptr};
     const auto *ck = p->chunk_kind[chunk];
     int rc;
-    if ((rc = launch_qt_list<kBluestein>(p, q2, nb, mo, b0, p->d_chunk_list + ck[1].off, ck[1].n, ck[1].len, st)))
-        return rc;
-    if ((rc = launch_qt_list<kDirect>(p, q2, nb, mo, b0, p->d_chunk_list + ck[0].off, ck[0].n, ck[0].len, st)))
-        return rc;
-    return launch_qt_list<kDirectBig>(p, q2, nb, mo, b0, p->d_chunk_list + ck[2].off, ck[2].n, ck[2].len, st);
+    if ((rc = launch_qt_list<kBluestein>(p, q2, nb, mo, b0, ck[1], st))) return rc;
+    if ((rc = launch_qt_list<kDirect>(p, q2, nb, mo, b0, ck[0], st))) return rc;
+    return launch_qt_list<kDirectBig>(p, q2, nb, mo, b0, ck[2], st);
 }
 
 int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, double *const *map_of_map,

@@ -141,6 +141,7 @@ int plan_save(shtb_plan_s *p, const char *path)
     Writer w{f};
     w.val(p->nrings); w.val(p->nhalf); w.val(p->npix); w.val(p->nalm);
     w.val(p->max_K_direct); w.val(p->max_M_mx); w.val(p->max_K_big); w.val(p->max_K_pow2); w.val(p->max_M_blue);
+    w.val(p->blue_split); w.val(p->max_M_small);
     w.val(p->chunk_kind); w.val(p->chunk_pix); w.val(p->stats);
     w.vec(p->ring_J); w.vec(p->ring_s); w.vec(p->ring_M); w.vec(p->ring_start);
     w.vec(p->direct_rings); w.vec(p->blue_rings); w.vec(p->big_rings);
@@ -209,14 +210,16 @@ int plan_load(shtb_plan_s *p, const char *path)
     const uint64_t big = 1ULL << 40;
     r.val(p->nrings); r.val(p->nhalf); r.val(p->npix); r.val(p->nalm);
     r.val(p->max_K_direct); r.val(p->max_M_mx); r.val(p->max_K_big); r.val(p->max_K_pow2); r.val(p->max_M_blue);
+    r.val(p->blue_split); r.val(p->max_M_small);
     r.val(p->chunk_kind); r.val(p->chunk_pix);
     shtb_plan_stats_t st{};
     r.val(st);
     r.vec(p->ring_J, big); r.vec(p->ring_s, big); r.vec(p->ring_M, big); r.vec(p->ring_start, big);
     r.vec(p->direct_rings, big); r.vec(p->blue_rings, big); r.vec(p->big_rings, big);
+    if (r.ok && (p->blue_split < 0 || p->blue_split > (int)p->blue_rings.size())) r.ok = false;
     for (const auto &row : p->chunk_kind)
         for (const auto &ck : row)
-            if (ck.n < 0 || ck.off < 0) r.ok = false;
+            if (ck.n < 0 || ck.off < 0 || ck.split < 0 || ck.split > ck.n) r.ok = false;
     r.val(p->view);
     int compressed = 0;
     r.val(compressed);

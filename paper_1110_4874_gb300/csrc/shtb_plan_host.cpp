@@ -673,6 +673,11 @@ int shtb_build_dense_plan(shtb_plan_s *p)
                          [&](int a, int b) { return p->ring_J[a] > p->ring_J[b]; });
         std::stable_sort(p->blue_rings.begin(), p->blue_rings.end(),
                          [&](int a, int b) { return ring_mx[a] > ring_mx[b]; });
+        constexpr int kSmallM = shtb_plan_s::kBlueSmallM;
+        p->blue_split = 0;
+        while (p->blue_split < (int)p->blue_rings.size() && ring_mx[p->blue_rings[p->blue_split]] > kSmallM)
+            ++p->blue_split;
+        p->max_M_small = p->blue_split < (int)p->blue_rings.size() ? ring_mx[p->blue_rings[p->blue_split]] : 0;
         // chunks of consecutive rings with about equal pixel counts
         constexpr int NCH = shtb_plan_s::kPhiChunks;
         std::vector<int> chunk_of(p->nrings);
@@ -693,10 +698,15 @@ int shtb_build_dense_plan(shtb_plan_s *p)
                 auto &ck = p->chunk_kind[cc][k];
                 ck.off = (int)chunk_list.size();
                 ck.len = 0;
+                ck.split = 0;
+                ck.len_small = 0;
                 for (int r : *lists[k])
                     if (chunk_of[r] == cc) {
                         chunk_list.push_back(r);
-                        ck.len = std::max(ck.len, k == 1 ? ring_mx[r] : p->ring_J[r] / 2);
+                        const int len = k == 1 ? ring_mx[r] : p->ring_J[r] / 2;
+                        ck.len = std::max(ck.len, len);
+                        if (k == 1 && len <= kSmallM) ck.len_small = std::max(ck.len_small, len);
+                        else ++ck.split;              // lists are sorted longest first
                     }
                 ck.n = (int)chunk_list.size() - ck.off;
             }

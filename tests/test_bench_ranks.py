@@ -1,0 +1,72 @@
+"""The N > 1 host logic of bench.py on CPU: replicas on gloo ranks agree on
+the slowest rank's time, the whole-job figure counts every rank's maps, and
+the reference arm runs on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        slowest = bench.reduce_max(10.0 + 5.0 * rank, dist, "cpu")
+        q.put((rank, slowest, bench.ms_per_map(slowest, 3, 8, world)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        got = sorted(q.get(timeout=120) for _ in range(2))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+    assert [p.exitcode for p in procs] == [0, 0]
+    # both ranks see rank 1's 15 ms; 2 ranks x 3 steps x 8 maps share it
+    assert got == [(0, 15.0, 15.0 / 48), (1, 15.0, 15.0 / 48)]
+
+
+def test_single_process_needs_no_group():
+    assert bench.reduce_max(7.5, None, "cpu") == 7.5
+    assert bench.ms_per_map(100.0, 2, 5, 1) == 10.0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("warmup", [0, 2])
+def test_bench_rejects_short_warmup(warmup):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", str(warmup)],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "warmup" in r.stderr
