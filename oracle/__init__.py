@@ -25,6 +25,10 @@ compression" (arXiv 1110.4874) that it follows:
   (Y^T f)_lm = 2 sum_p f_p P_l^m(z_p) e^{-i m phi_p} for m >= 1.
 * ``analyze`` -- spherical-harmonic analysis by the ring quadrature of Eq.
   (sh-forward-quadrature), optionally refined by Jacobi steps.
+* ``spin_lambda``, ``spin_q``, ``spin_synthesize`` -- spin-weighted
+  harmonics and the polarised (spin-2) synthesis of Q and U maps from E and
+  B coefficients, the spin-weighted transforms of the paper's Discussion
+  (Sec. 5), from the Wigner-d closed form.
 
 Parity of every function here is pinned by ``tests/test_oracle_pins.py``.
 """
@@ -93,6 +97,11 @@ def _load():
                                                  ctypes.c_int]
             lib.orc_adjoint.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, _IP, _IP,
                                         ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int]
+            lib.orc_spin_lambda.restype = None
+            lib.orc_spin_lambda.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]
+            lib.orc_spin_q.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_int,
+                                       _DP, _DP, _DP, _DP, ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -317,3 +326,41 @@ def analyze(rings: Rings, lmax: int, maps, ring_weight, niter: int = 0,
     for _ in range(niter):
         a = a + quad(f - synthesize(rings, lmax, a, nthreads))
     return a
+
+
+def spin_lambda(s: int, m: int, lmax: int, z: float, sinth: float | None = None) -> np.ndarray:
+    """s_lambda_lm(z) for l = 0..lmax (0 below l = max(|m|, |s|)):
+    (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta), the spin-s harmonic without
+    its e^{i m phi} (Newman-Penrose convention; s = 0 gives Eq. Y-def).
+    Any integer m in [-lmax, lmax]."""
+    zz = np.array([z], dtype=np.float64)
+    st, sl = np.empty(1), np.empty(1)
+    _load().orc_sin_from_cos(1, _dp(zz), _dp(st), _dp(sl))
+    if sinth is not None:
+        st[0], sl[0] = sinth, 0.0
+    out = np.zeros(lmax + 1)
+    _load().orc_spin_lambda(int(s), int(m), int(lmax), float(z), 0.0, float(st[0]), float(sl[0]), _dp(out))
+    return out
+
+
+def spin_q(rings: Rings, lmax: int, alm_E, alm_B, nthreads: int = 0):
+    """Polarised Legendre stage, HEALPix convention
+    Q + iU = -sum (a_E + i a_B) 2Y and Q - iU = -sum (a_E - i a_B) (-2)Y:
+    Q_m(z_k) = -sum_l [a_E F+ + i a_B F-] and U_m(z_k) = -sum_l [a_B F+ -
+    i a_E F-], F+- = (2_lambda +- (-2)_lambda)/2.  Returns (qQ, qU), each
+    complex [nmaps, nrings, lmax+1]; the maps follow from ``phi_synth``."""
+    e, nmaps = _alm2d(alm_E, lmax)
+    b, nb = _alm2d(alm_B, lmax)
+    assert nb == nmaps
+    qQ = np.zeros((nmaps, rings.nrings, lmax + 1), dtype=np.complex128)
+    qU = np.zeros_like(qQ)
+    rc = _load().orc_spin_q(rings.nrings, *rings._geo(), lmax, nmaps, _dp(e), _dp(b),
+                            _dp(qQ.view(np.float64)), _dp(qU.view(np.float64)), nthreads)
+    assert rc == 0
+    return qQ, qU
+
+
+def spin_synthesize(rings: Rings, lmax: int, alm_E, alm_B, nthreads: int = 0):
+    """Q and U maps (real [nmaps, npix] each) of the E and B coefficients."""
+    qQ, qU = spin_q(rings, lmax, alm_E, alm_B, nthreads)
+    return phi_synth(rings, lmax, qQ, nthreads), phi_synth(rings, lmax, qU, nthreads)

@@ -587,6 +587,163 @@ int orc_adjoint(int nrings, const double *z, const double *zlo, const double *si
     return rc;
 }
 
+/* ------------------------------------------------ spin-weighted functions */
+/*
+ * Spin-weighted harmonics, for the polarised transform the paper points to
+ * (Sec. 5, "spin-weighted spherical harmonic transforms"):
+ *   sY_lm(theta, phi) = s_lambda_lm(theta) e^{i m phi},
+ *   s_lambda_lm(theta) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta),
+ * with d^l_{m1 m2}(theta) = <l m1| exp(-i theta J_y) |l m2> the Wigner
+ * small-d function.  This is the Newman-Penrose convention, in which the
+ * spin-raising operator takes s_Y to (s+1)_Y; at s = 0 it is Eq. (Y-def)
+ * with the Condon-Shortley phase.  d is evaluated from its closed form in
+ * Jacobi polynomials (DLMF 18.5, Varshalovich et al. Sec. 4.3.4): with
+ * k = min(l+m2, l-m2, l+m1, l-m1) and, by which of the four attains k,
+ *   a = |m1 - m2|, b = 2l - 2k - a, sign (-1)^(m1-m2) when k = l+m2 or
+ *   l-m1 (else +1),
+ *   d = sign sqrt(C(2l-k, k+a) / C(k+b, b)) sin(theta/2)^a cos(theta/2)^b
+ *       P_k^(a,b)(cos theta),
+ * P_k^(a,b) by its three-term recurrence in the degree (DLMF 18.9.1), all in
+ * long double.  This is a different route from the product path's plan
+ * builder, which runs the Wigner recurrence in l.
+ */
+static long double jacobi_p(int n, long double a, long double b, long double x)
+{
+    long double p0 = 1.0L;
+    if (n == 0) return p0;
+    long double p1 = (a + 1.0L) + 0.5L * (a + b + 2.0L) * (x - 1.0L);
+    for (int k = 2; k <= n; ++k) {
+        const long double c = 2.0L * k + a + b;
+        const long double p2 = ((c - 1.0L) * (c * (c - 2.0L) * x + a * a - b * b) * p1 -
+                                2.0L * (k + a - 1.0L) * (k + b - 1.0L) * c * p0) /
+                               (2.0L * k * (k + a + b) * (c - 2.0L));
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+static long double log_binom(int n, int r)
+{
+    return lgammal(n + 1.0L) - lgammal(r + 1.0L) - lgammal(n - r + 1.0L);
+}
+
+/* d^l_{m1 m2}(theta) from cos(theta) and the half-angle sines/cosines */
+static long double wigner_d(int l, int m1, int m2, long double x, long double sh, long double ch)
+{
+    const int k1 = l + m2, k2 = l - m2, k3 = l + m1, k4 = l - m1;
+    int k = k1, a, sgn;
+    if (k2 < k) k = k2;
+    if (k3 < k) k = k3;
+    if (k4 < k) k = k4;
+    if (k < 0) return 0.0L;
+    if (k == k1) { a = m1 - m2; sgn = (a & 1) ? -1 : 1; }
+    else if (k == k2) { a = m2 - m1; sgn = 1; }
+    else if (k == k3) { a = m2 - m1; sgn = 1; }
+    else { a = m1 - m2; sgn = (a & 1) ? -1 : 1; }
+    const int b = 2 * l - 2 * k - a;
+    const long double lp = 0.5L * (log_binom(2 * l - k, k + a) - log_binom(k + b, b)) +
+                           (a ? a * logl(sh) : 0.0L) + (b ? b * logl(ch) : 0.0L);
+    if (lp < -11000.0L) return 0.0L;
+    return sgn * expl(lp) * jacobi_p(k, a, b, x);
+}
+
+/* half-angle sine and cosine from cos(theta), sin(theta) (double-double
+   inputs), without cancellation on either hemisphere */
+static void half_angles(dd z, dd st, long double *sh, long double *ch)
+{
+    const long double zz = (long double)z.hi + z.lo, ss = (long double)st.hi + st.lo;
+    if (zz >= 0) {
+        *ch = sqrtl(0.5L * (1.0L + zz));
+        *sh = ss / (2.0L * *ch);
+    } else {
+        *sh = sqrtl(0.5L * (1.0L - zz));
+        *ch = ss / (2.0L * *sh);
+    }
+}
+
+/* s_lambda_lm at one point for l = 0..lmax (0 where l < max(|m|, |s|)) */
+static void spin_lambda_eval(int s, int m, int lmax, dd z, dd st, long double *out)
+{
+    long double sh, ch;
+    half_angles(z, st, &sh, &ch);
+    const long double x = (long double)z.hi + z.lo;
+    const int l0 = abs(m) > abs(s) ? abs(m) : abs(s);
+    const long double sign = (s & 1) ? -1.0L : 1.0L;
+    for (int l = 0; l <= lmax; ++l)
+        out[l] = l < l0 ? 0.0L
+                        : sign * sqrtl((2.0L * l + 1.0L) / (4.0L * 3.14159265358979323846264338327950288L)) *
+                              wigner_d(l, m, -s, x, sh, ch);
+}
+
+void orc_spin_lambda(int s, int m, int lmax, double z, double zlo, double sinth, double sinlo,
+                     double *out)
+{
+    long double *v = (long double *)malloc(sizeof(long double) * (size_t)(lmax + 1));
+    const dd zz = {z, zlo}, ss = {sinth, sinlo};
+    spin_lambda_eval(s, m, lmax, zz, ss, v);
+    for (int l = 0; l <= lmax; ++l) out[l] = (double)v[l];
+    free(v);
+}
+
+/*
+ * Polarised (spin-2) Legendre stage at the given rings, HEALPix convention
+ * (Q + iU) = -sum (aE + i aB) 2Y, (Q - iU) = -sum (aE - i aB) (-2)Y:
+ * with F+- = (2_lambda +- (-2)_lambda)/2,
+ *   Q_m(z) = -sum_l [aE F+ + i aB F-],   U_m(z) = -sum_l [aB F+ - i aE F-],
+ * so that Q = Re Q_0 + 2 sum_{m>=1} Re(Q_m e^{i m phi}) and the same for U
+ * (both maps real).  qQ, qU: [nmaps][nrings][lmax+1] complex.
+ */
+int orc_spin_q(int nrings, const double *z, const double *zlo, const double *sinth,
+               const double *sinlo, int lmax, int nmaps, const double *aE, const double *aB,
+               double *qQ, double *qU, int nthreads)
+{
+    if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
+    const long long nalm = orc_nalm(lmax);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        long double *lp = (long double *)malloc(sizeof(long double) * (size_t)(lmax + 1));
+        long double *lm = (long double *)malloc(sizeof(long double) * (size_t)(lmax + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int k = 0; k < nrings; ++k) {
+            const dd zk = {z[k], zlo[k]}, sk = {sinth[k], sinlo[k]};
+            for (int m = 0; m <= lmax; ++m) {
+                spin_lambda_eval(2, m, lmax, zk, sk, lp);
+                spin_lambda_eval(-2, m, lmax, zk, sk, lm);
+                for (int b = 0; b < nmaps; ++b) {
+                    const double *e = aE + 2 * (size_t)nalm * b, *bb = aB + 2 * (size_t)nalm * b;
+                    long double qr = 0, qi = 0, ur = 0, ui = 0;
+                    for (int l = m; l <= lmax; ++l) {
+                        const long long idx = alm_index(lmax, l, m);
+                        const long double Fp = 0.5L * (lp[l] + lm[l]), Fm = 0.5L * (lp[l] - lm[l]);
+                        const long double er = e[2 * idx], ei = m ? e[2 * idx + 1] : 0.0;
+                        const long double br = bb[2 * idx], bi = m ? bb[2 * idx + 1] : 0.0;
+                        /* Q_m -= aE F+ + i aB F-;  U_m -= aB F+ - i aE F- */
+                        qr -= er * Fp - bi * Fm;
+                        qi -= ei * Fp + br * Fm;
+                        ur -= br * Fp + ei * Fm;
+                        ui -= bi * Fp - er * Fm;
+                    }
+                    double *qo = qQ + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
+                    double *uo = qU + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
+                    qo[0] = (double)qr;
+                    qo[1] = (double)qi;
+                    uo[0] = (double)ur;
+                    uo[1] = (double)ui;
+                }
+            }
+        }
+        free(lp);
+        free(lm);
+    }
+    return 0;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -404,3 +404,138 @@ def test_legendre_stage_matches_full_synthesis_on_ring_subset():
     part = oracle.synthesize(sub, lmax, a)
     want = np.concatenate([full[:, rings.start[k]:rings.start[k + 1]] for k in idx], axis=1)
     np.testing.assert_array_equal(part, want)
+
+
+# ------------------------------------------------------ spin-weighted (s = +-2)
+def test_spin_zero_is_the_scalar_legendre_function():
+    """At s = 0 the spin-weighted function is Eq. (Y-def) with the
+    Condon-Shortley phase: the Wigner-d route equals the scalar recurrence."""
+    for z in (0.97, 0.3, -0.55, 0.999):
+        for m in (0, 1, 2, 7, 20):
+            want = oracle.legendre(m, 40, z)
+            got = oracle.spin_lambda(0, m, 40, z)[m:]
+            np.testing.assert_allclose(got, want, rtol=0, atol=1e-14 * max(1.0, np.abs(want).max()))
+
+
+def test_spin_two_closed_forms():
+    """l = 2 spin-2 harmonics, obtained by applying the spin-raising operator
+    twice to Y_2m (Newman-Penrose convention):
+    2Y_22 = sqrt(5/pi)/8 (1 - cos)^2, 2Y_21 = -sqrt(5/pi)/4 sin (1 - cos),
+    2Y_20 = sqrt(15/(2 pi))/4 sin^2, 2Y_2,-2 = sqrt(5/pi)/8 (1 + cos)^2."""
+    for th in (0.2, 0.7, 1.9, 2.8):
+        z, s = math.cos(th), math.sin(th)
+        want = {2: math.sqrt(5 / math.pi) / 8 * (1 - z) ** 2,
+                1: -math.sqrt(5 / math.pi) / 4 * s * (1 - z),
+                0: math.sqrt(15 / (2 * math.pi)) / 4 * s * s,
+                -2: math.sqrt(5 / math.pi) / 8 * (1 + z) ** 2}
+        for m, w in want.items():
+            assert oracle.spin_lambda(2, m, 2, z)[2] == pytest.approx(w, rel=1e-14, abs=1e-16)
+
+
+def _eth(f, s, m, th, h=1e-5):
+    """Spin raising (Newman-Penrose): -(sin)^s [d/dth - m/sin] (sin^-s f)."""
+    g = lambda t: f(t) / math.sin(t) ** s  # noqa: E731
+    dg = (g(th + h) - g(th - h)) / (2 * h)
+    return -(math.sin(th) ** s) * (dg - m / math.sin(th) * g(th))
+
+
+def _eth_bar(f, s, m, th, h=1e-5):
+    """Spin lowering: -(sin)^-s [d/dth + m/sin] (sin^s f)."""
+    g = lambda t: f(t) * math.sin(t) ** s  # noqa: E731
+    dg = (g(th + h) - g(th - h)) / (2 * h)
+    return -(math.sin(th) ** (-s)) * (dg + m / math.sin(th) * g(th))
+
+
+def test_spin_raising_and_lowering_relations():
+    """(s+1)Y_lm = eth sY_lm / sqrt((l-s)(l+s+1)) and (s-1)Y_lm =
+    -eth_bar sY_lm / sqrt((l+s)(l-s+1)), by central differences in theta:
+    this fixes the sign convention of every spin relative to s = 0."""
+    def lam(s, l, m):
+        return lambda t: oracle.spin_lambda(s, m, l, math.cos(t), math.sin(t))[l]
+    for th in (0.4, 1.3, 2.5):
+        for l, m in ((3, 0), (4, 1), (5, 2), (6, -3), (7, 5), (9, -8)):
+            for s in (0, 1):
+                up = _eth(lam(s, l, m), s, m, th) / math.sqrt((l - s) * (l + s + 1))
+                assert up == pytest.approx(lam(s + 1, l, m)(th), abs=1e-8)
+            for s in (0, -1):
+                dn = -_eth_bar(lam(s, l, m), s, m, th) / math.sqrt((l + s) * (l - s + 1))
+                assert dn == pytest.approx(lam(s - 1, l, m)(th), abs=1e-8)
+
+
+@pytest.mark.parametrize("s", [-2, -1, 1, 2])
+def test_spin_addition_theorem(s):
+    """sum_m |sY_lm|^2 = (2l+1)/(4 pi) for every spin weight."""
+    lmax = 40
+    for z in (0.999, 0.6, -0.2, -0.9):
+        tot = np.zeros(lmax + 1)
+        for m in range(-lmax, lmax + 1):
+            tot += oracle.spin_lambda(s, m, lmax, z) ** 2
+        ls = np.arange(abs(s), lmax + 1)
+        np.testing.assert_allclose(tot[abs(s):], (2 * ls + 1) / (4 * math.pi), rtol=1e-13)
+
+
+def test_spin_parity_and_negative_m():
+    """s_lambda_lm(-z) = (-1)^(l+m) (-s)_lambda_lm(z) and
+    s_lambda_l,-m = (-1)^(s+m) (-s)_lambda_lm."""
+    lmax = 30
+    for z in (0.8, 0.15):
+        for m in (0, 1, 2, 5, 17):
+            for s in (2, -2):
+                a = oracle.spin_lambda(s, m, lmax, -z)
+                b = oracle.spin_lambda(-s, m, lmax, z)
+                sign = np.array([(-1) ** (l + m) for l in range(lmax + 1)])
+                np.testing.assert_allclose(a, sign * b, atol=1e-15)
+                c = oracle.spin_lambda(s, -m, lmax, z)
+                np.testing.assert_allclose(c, (-1) ** (s + m) * b, atol=1e-15)
+
+
+def test_spin_gauss_legendre_orthonormality():
+    """2 pi sum_k w_k 2lambda_lm(z_k) 2lambda_l'm(z_k) = delta_ll' for
+    2 <= l, l' <= L on L+1 Gauss-Legendre nodes (the products are
+    polynomials of degree <= 2L in z)."""
+    lmax = 16
+    rings, w = oracle.gauss_legendre_rings(lmax + 1, 2 * lmax + 1)
+    for m in range(0, lmax + 1):
+        P = np.array([oracle.spin_lambda(2, m, lmax, z, s) for z, s in zip(rings.z, rings.sinth)])
+        l0 = max(m, 2)
+        G = 2 * math.pi * (P[:, l0:].T * w) @ P[:, l0:]
+        np.testing.assert_allclose(G, np.eye(lmax + 1 - l0), atol=2e-14)
+
+
+def test_polarised_single_modes_brute_force():
+    """One coefficient at a time, pixel by pixel: a_E,lm = 1 gives
+    Q = -2 F+ cos(m phi), U = -2 F- sin(m phi); a_B,lm = 1 gives
+    Q = 2 F- sin(m phi), U = -2 F+ cos(m phi) (m >= 1; F+- = (2_lambda +-
+    (-2)_lambda)/2); at m = 0, a_E,l0 = 1 gives Q = -F+, U = 0."""
+    nside, lmax = 4, 8
+    rings = oracle.healpix_rings(nside)
+    z, phi = _expand(rings)
+    for l, m in ((2, 0), (3, 1), (5, 2), (8, 7)):
+        for which in ("E", "B"):
+            aE = np.zeros(oracle.nalm(lmax), dtype=np.complex128)
+            aB = np.zeros_like(aE)
+            (aE if which == "E" else aB)[_alm_index(lmax, l, m)] = 1.0
+            Q, U = oracle.spin_synthesize(rings, lmax, aE, aB)
+            Fp = np.array([0.5 * (oracle.spin_lambda(2, m, lmax, zz)[l] + oracle.spin_lambda(-2, m, lmax, zz)[l])
+                           for zz in z])
+            Fm = np.array([0.5 * (oracle.spin_lambda(2, m, lmax, zz)[l] - oracle.spin_lambda(-2, m, lmax, zz)[l])
+                           for zz in z])
+            c = 1.0 if m == 0 else 2.0
+            if which == "E":
+                wantQ, wantU = -c * Fp * np.cos(m * phi), -c * Fm * np.sin(m * phi)
+            else:
+                wantQ, wantU = c * Fm * np.sin(m * phi), -c * Fp * np.cos(m * phi)
+            np.testing.assert_allclose(Q[0], wantQ, atol=1e-14)
+            np.testing.assert_allclose(U[0], wantU, atol=1e-14)
+
+
+def test_polarised_rotation_of_e_into_b():
+    """(a_E, a_B) -> (-a_B, a_E) multiplies Q + iU by i: (Q, U) -> (-U, Q)."""
+    nside, lmax = 8, 16
+    rings = oracle.healpix_rings(nside)
+    aE = _random_alm(lmax, 2, 51)
+    aB = _random_alm(lmax, 2, 52)
+    Q, U = oracle.spin_synthesize(rings, lmax, aE, aB)
+    Q2, U2 = oracle.spin_synthesize(rings, lmax, -aB, aE)
+    np.testing.assert_allclose(Q2, -U, atol=1e-13)
+    np.testing.assert_allclose(U2, Q, atol=1e-13)
