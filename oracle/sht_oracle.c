@@ -607,45 +607,23 @@ int orc_adjoint(int nrings, const double *z, const double *zlo, const double *si
  * long double.  This is a different route from the product path's plan
  * builder, which runs the Wigner recurrence in l.
  */
-static long double jacobi_p(int n, long double a, long double b, long double x)
+/* P_k^(a,b)(x) for k = 0..n into p[0..n] */
+static void jacobi_all(int n, long double a, long double b, long double x, long double *p)
 {
-    long double p0 = 1.0L;
-    if (n == 0) return p0;
-    long double p1 = (a + 1.0L) + 0.5L * (a + b + 2.0L) * (x - 1.0L);
+    p[0] = 1.0L;
+    if (n == 0) return;
+    p[1] = (a + 1.0L) + 0.5L * (a + b + 2.0L) * (x - 1.0L);
     for (int k = 2; k <= n; ++k) {
         const long double c = 2.0L * k + a + b;
-        const long double p2 = ((c - 1.0L) * (c * (c - 2.0L) * x + a * a - b * b) * p1 -
-                                2.0L * (k + a - 1.0L) * (k + b - 1.0L) * c * p0) /
-                               (2.0L * k * (k + a + b) * (c - 2.0L));
-        p0 = p1;
-        p1 = p2;
+        p[k] = ((c - 1.0L) * (c * (c - 2.0L) * x + a * a - b * b) * p[k - 1] -
+                2.0L * (k + a - 1.0L) * (k + b - 1.0L) * c * p[k - 2]) /
+               (2.0L * k * (k + a + b) * (c - 2.0L));
     }
-    return p1;
 }
 
 static long double log_binom(int n, int r)
 {
     return lgammal(n + 1.0L) - lgammal(r + 1.0L) - lgammal(n - r + 1.0L);
-}
-
-/* d^l_{m1 m2}(theta) from cos(theta) and the half-angle sines/cosines */
-static long double wigner_d(int l, int m1, int m2, long double x, long double sh, long double ch)
-{
-    const int k1 = l + m2, k2 = l - m2, k3 = l + m1, k4 = l - m1;
-    int k = k1, a, sgn;
-    if (k2 < k) k = k2;
-    if (k3 < k) k = k3;
-    if (k4 < k) k = k4;
-    if (k < 0) return 0.0L;
-    if (k == k1) { a = m1 - m2; sgn = (a & 1) ? -1 : 1; }
-    else if (k == k2) { a = m2 - m1; sgn = 1; }
-    else if (k == k3) { a = m2 - m1; sgn = 1; }
-    else { a = m1 - m2; sgn = (a & 1) ? -1 : 1; }
-    const int b = 2 * l - 2 * k - a;
-    const long double lp = 0.5L * (log_binom(2 * l - k, k + a) - log_binom(k + b, b)) +
-                           (a ? a * logl(sh) : 0.0L) + (b ? b * logl(ch) : 0.0L);
-    if (lp < -11000.0L) return 0.0L;
-    return sgn * expl(lp) * jacobi_p(k, a, b, x);
 }
 
 /* half-angle sine and cosine from cos(theta), sin(theta) (double-double
@@ -662,18 +640,47 @@ static void half_angles(dd z, dd st, long double *sh, long double *ch)
     }
 }
 
-/* s_lambda_lm at one point for l = 0..lmax (0 where l < max(|m|, |s|)) */
+/* s_lambda_lm at one point for l = 0..lmax (0 where l < max(|m|, |s|)).
+   For fixed (m1, m2) = (m, -s) the case of the closed form, hence (a, b)
+   and the sign, is the same for every l >= l0 = max(|m1|, |m2|), and
+   k = l - l0, so one pass of the degree recurrence serves all l. */
 static void spin_lambda_eval(int s, int m, int lmax, dd z, dd st, long double *out)
 {
+    for (int l = 0; l <= lmax; ++l) out[l] = 0.0L;
+    const int m1 = m, m2 = -s;
+    const int l0 = abs(m1) > abs(m2) ? abs(m1) : abs(m2);
+    if (l0 > lmax) return;
     long double sh, ch;
     half_angles(z, st, &sh, &ch);
     const long double x = (long double)z.hi + z.lo;
-    const int l0 = abs(m) > abs(s) ? abs(m) : abs(s);
-    const long double sign = (s & 1) ? -1.0L : 1.0L;
-    for (int l = 0; l <= lmax; ++l)
-        out[l] = l < l0 ? 0.0L
-                        : sign * sqrtl((2.0L * l + 1.0L) / (4.0L * 3.14159265358979323846264338327950288L)) *
-                              wigner_d(l, m, -s, x, sh, ch);
+    /* which of l+m2, l-m2, l+m1, l-m1 is smallest (they differ by l-free amounts) */
+    const int k1 = m2, k2 = -m2, k3 = m1, k4 = -m1;
+    int kk = k1, a, sgn;
+    if (k2 < kk) kk = k2;
+    if (k3 < kk) kk = k3;
+    if (k4 < kk) kk = k4;
+    if (kk == k1) { a = m1 - m2; sgn = (a & 1) ? -1 : 1; }
+    else if (kk == k2) { a = m2 - m1; sgn = 1; }
+    else if (kk == k3) { a = m2 - m1; sgn = 1; }
+    else { a = m1 - m2; sgn = (a & 1) ? -1 : 1; }
+    const int n = lmax - l0;
+    long double *p = (long double *)malloc(sizeof(long double) * (size_t)(n + 1));
+    const long double lsh = logl(sh), lch = logl(ch);
+    const long double sign_s = (s & 1) ? -1.0L : 1.0L;
+    const long double four_pi = 4.0L * 3.14159265358979323846264338327950288L;
+    int b0 = -1;
+    for (int l = l0; l <= lmax; ++l) {
+        const int k = l - l0, b = 2 * l - 2 * k - a;
+        if (b0 < 0) {                   /* b = 2 l0 - a is the same for every l */
+            b0 = b;
+            jacobi_all(n, a, b, x, p);
+        }
+        const long double lp = 0.5L * (log_binom(2 * l - k, k + a) - log_binom(k + b, b)) +
+                               (a ? a * lsh : 0.0L) + (b ? b * lch : 0.0L);
+        const long double d = lp < -11000.0L ? 0.0L : sgn * expl(lp) * p[k];
+        out[l] = sign_s * sqrtl((2.0L * l + 1.0L) / four_pi) * d;
+    }
+    free(p);
 }
 
 void orc_spin_lambda(int s, int m, int lmax, double z, double zlo, double sinth, double sinlo,
