@@ -25,10 +25,10 @@ compression" (arXiv 1110.4874) that it follows:
   (Y^T f)_lm = 2 sum_p f_p P_l^m(z_p) e^{-i m phi_p} for m >= 1.
 * ``analyze`` -- spherical-harmonic analysis by the ring quadrature of Eq.
   (sh-forward-quadrature), optionally refined by Jacobi steps.
-* ``spin_lambda``, ``spin_q``, ``spin_synthesize`` -- spin-weighted
-  harmonics and the polarised (spin-2) synthesis of Q and U maps from E and
-  B coefficients, the spin-weighted transforms of the paper's Discussion
-  (Sec. 5), from the Wigner-d closed form.
+* ``spin_lambda``, ``spin_q``, ``spin_synthesize``, ``spin_adjoint`` --
+  spin-weighted harmonics, the polarised (spin-2) synthesis of Q and U maps
+  from E and B coefficients (the spin-weighted transforms of the paper's
+  Discussion, Sec. 5) from the Wigner-d closed form, and its transpose.
 
 Parity of every function here is pinned by ``tests/test_oracle_pins.py``.
 """
@@ -102,6 +102,8 @@ def _load():
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]
             lib.orc_spin_q.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_int,
                                        _DP, _DP, _DP, _DP, ctypes.c_int]
+            lib.orc_spin_legendre_adjoint.argtypes = [ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int,
+                                                      ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -364,3 +366,22 @@ def spin_synthesize(rings: Rings, lmax: int, alm_E, alm_B, nthreads: int = 0):
     """Q and U maps (real [nmaps, npix] each) of the E and B coefficients."""
     qQ, qU = spin_q(rings, lmax, alm_E, alm_B, nthreads)
     return phi_synth(rings, lmax, qQ, nthreads), phi_synth(rings, lmax, qU, nthreads)
+
+
+def spin_adjoint(rings: Rings, lmax: int, Q, U, nthreads: int = 0):
+    """Transpose of ``spin_synthesize`` under real inner products over the
+    (Re, Im) pairs of a_E and a_B: returns (g_E, g_B), complex [nmaps, nalm],
+    with <spin_synthesize(a_E, a_B), (Q, U)> = <a_E, g_E> + <a_B, g_B>.
+    The ring sums are ``phi_adjoint``; the Legendre part is the transposed
+    combine, g_E = c_m sum_k [-F+ G_Q - i F- G_U] and g_B = c_m sum_k
+    [i F- G_Q - F+ G_U] (c_0 = 1, c_m = 2)."""
+    GQ = phi_adjoint(rings, lmax, Q, nthreads)
+    GU = phi_adjoint(rings, lmax, U, nthreads)
+    nmaps = GQ.shape[0]
+    gE = np.zeros((nmaps, nalm(lmax)), dtype=np.complex128)
+    gB = np.zeros_like(gE)
+    rc = _load().orc_spin_legendre_adjoint(rings.nrings, *rings._geo(), lmax, nmaps,
+                                           _dp(GQ.view(np.float64)), _dp(GU.view(np.float64)),
+                                           _dp(gE.view(np.float64)), _dp(gB.view(np.float64)), nthreads)
+    assert rc == 0
+    return gE, gB

@@ -751,6 +751,71 @@ int orc_spin_q(int nrings, const double *z, const double *zlo, const double *sin
     return 0;
 }
 
+/*
+ * Transpose of the polarised Legendre stage under real inner products over
+ * (Re, Im) pairs: given GQ_m(k), GU_m(k) = sum_j f_kj e^{-i m phi_kj} of the
+ * Q and U maps (orc_phi_adjoint), and c_0 = 1, c_m = 2 (the -m terms),
+ *   gE_lm = c_m sum_k [-F+ GQ - i F- GU],   gB_lm = c_m sum_k [i F- GQ - F+ GU],
+ * the derivatives of sum_p (Q'_p Q_p + U'_p U_p) with respect to Re and Im
+ * of aE_lm and aB_lm (written as Re + i Im).  Im of the m = 0 entries is 0.
+ */
+int orc_spin_legendre_adjoint(int nrings, const double *z, const double *zlo, const double *sinth,
+                              const double *sinlo, int lmax, int nmaps, const double *GQ,
+                              const double *GU, double *gE, double *gB, int nthreads)
+{
+    if (nrings < 0 || lmax < 0 || nmaps < 1) return -1;
+    const long long nalm = orc_nalm(lmax);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        long double *lp = (long double *)malloc(sizeof(long double) * (size_t)(lmax + 1));
+        long double *lm = (long double *)malloc(sizeof(long double) * (size_t)(lmax + 1));
+        long double *acc = (long double *)malloc(sizeof(long double) * 4 * (size_t)(lmax + 1) * nmaps);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int m = 0; m <= lmax; ++m) {
+            memset(acc, 0, sizeof(long double) * 4 * (size_t)(lmax + 1) * nmaps);
+            for (int k = 0; k < nrings; ++k) {
+                const dd zk = {z[k], zlo[k]}, sk = {sinth[k], sinlo[k]};
+                spin_lambda_eval(2, m, lmax, zk, sk, lp);
+                spin_lambda_eval(-2, m, lmax, zk, sk, lm);
+                for (int b = 0; b < nmaps; ++b) {
+                    const double *q = GQ + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
+                    const double *u = GU + 2 * (((size_t)b * nrings + k) * (lmax + 1) + m);
+                    long double *ab = acc + 4 * (size_t)b * (lmax + 1);
+                    for (int l = m; l <= lmax; ++l) {
+                        const long double Fp = 0.5L * (lp[l] + lm[l]), Fm = 0.5L * (lp[l] - lm[l]);
+                        /* -F+ GQ - i F- GU  and  i F- GQ - F+ GU */
+                        ab[4 * l + 0] += -Fp * q[0] + Fm * u[1];
+                        ab[4 * l + 1] += -Fp * q[1] - Fm * u[0];
+                        ab[4 * l + 2] += -Fm * q[1] - Fp * u[0];
+                        ab[4 * l + 3] += Fm * q[0] - Fp * u[1];
+                    }
+                }
+            }
+            const long double c = m == 0 ? 1.0L : 2.0L;
+            for (int b = 0; b < nmaps; ++b) {
+                const long double *ab = acc + 4 * (size_t)b * (lmax + 1);
+                for (int l = m; l <= lmax; ++l) {
+                    const long long idx = alm_index(lmax, l, m);
+                    double *e = gE + 2 * ((size_t)nalm * b + idx), *bb = gB + 2 * ((size_t)nalm * b + idx);
+                    e[0] = (double)(c * ab[4 * l + 0]);
+                    e[1] = m ? (double)(c * ab[4 * l + 1]) : 0.0;
+                    bb[0] = (double)(c * ab[4 * l + 2]);
+                    bb[1] = m ? (double)(c * ab[4 * l + 3]) : 0.0;
+                }
+            }
+        }
+        free(lp);
+        free(lm);
+        free(acc);
+    }
+    return 0;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

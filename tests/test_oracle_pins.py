@@ -539,3 +539,47 @@ def test_polarised_rotation_of_e_into_b():
     Q2, U2 = oracle.spin_synthesize(rings, lmax, -aB, aE)
     np.testing.assert_allclose(Q2, -U, atol=1e-13)
     np.testing.assert_allclose(U2, Q, atol=1e-13)
+
+
+def test_polarised_adjoint_dot_product_identity():
+    """<Y_pol (a_E, a_B), (Q, U)> = <a_E, g_E> + <a_B, g_B> with real inner
+    products over (Re, Im); Im of the m = 0 outputs is 0."""
+    nside, lmax = 8, 16
+    rings = oracle.healpix_rings(nside)
+    aE = _random_alm(lmax, 2, 61)
+    aB = _random_alm(lmax, 2, 62)
+    rng = np.random.default_rng(63)
+    Q = rng.standard_normal((2, rings.npix))
+    U = rng.standard_normal((2, rings.npix))
+    Qa, Ua = oracle.spin_synthesize(rings, lmax, aE, aB)
+    gE, gB = oracle.spin_adjoint(rings, lmax, Q, U)
+    lhs = np.sum(Qa * Q + Ua * U)
+    rhs = np.sum(aE.real * gE.real + aE.imag * gE.imag + aB.real * gB.real + aB.imag * gB.imag)
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    m0 = [_alm_index(lmax, l, 0) for l in range(lmax + 1)]
+    assert np.all(gE[:, m0].imag == 0) and np.all(gB[:, m0].imag == 0)
+
+
+def test_polarised_adjoint_is_explicit_transpose():
+    """Dense polarised operator from synthesising every real unit
+    coefficient (Re and Im of a_E and a_B; Im a_l0 has no effect), compared
+    with the adjoint applied to every unit pixel of Q and U."""
+    nside, lmax = 2, 4
+    rings = oracle.healpix_rings(nside)
+    n = oracle.nalm(lmax)
+    cols = []
+    for field in range(2):
+        for part in (1.0, 1j):
+            for i in range(n):
+                a = [np.zeros(n, dtype=np.complex128), np.zeros(n, dtype=np.complex128)]
+                a[field][i] = part
+                Q, U = oracle.spin_synthesize(rings, lmax, a[0], a[1])
+                cols.append(np.concatenate([Q[0], U[0]]))
+    Y = np.array(cols).T                      # [2 npix, 4 nalm]
+    npix = rings.npix
+    eye = np.eye(2 * npix)
+    gE, gB = oracle.spin_adjoint(rings, lmax, eye[:, :npix], eye[:, npix:])
+    YT = np.concatenate([gE.real, gE.imag, gB.real, gB.imag], axis=1)   # [2 npix, 4 nalm]
+    m0 = np.array([m == 0 for m in range(lmax + 1) for _ in range(m, lmax + 1)])
+    keep = np.concatenate([np.ones(n, bool), ~m0, np.ones(n, bool), ~m0])
+    np.testing.assert_allclose(YT[:, keep], Y[:, keep], atol=1e-13)
