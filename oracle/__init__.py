@@ -25,10 +25,12 @@ compression" (arXiv 1110.4874) that it follows:
   (Y^T f)_lm = 2 sum_p f_p P_l^m(z_p) e^{-i m phi_p} for m >= 1.
 * ``analyze`` -- spherical-harmonic analysis by the ring quadrature of Eq.
   (sh-forward-quadrature), optionally refined by Jacobi steps.
-* ``spin_lambda``, ``spin_q``, ``spin_synthesize``, ``spin_adjoint`` --
+* ``spin_lambda``, ``spin_q``, ``spin_synthesize``, ``spin_adjoint``,
+  ``spin_analyze`` --
   spin-weighted harmonics, the polarised (spin-2) synthesis of Q and U maps
   from E and B coefficients (the spin-weighted transforms of the paper's
-  Discussion, Sec. 5) from the Wigner-d closed form, and its transpose.
+  Discussion, Sec. 5) from the Wigner-d closed form, its transpose, and the
+  quadrature analysis built on that transpose.
 
 Parity of every function here is pinned by ``tests/test_oracle_pins.py``.
 """
@@ -385,3 +387,27 @@ def spin_adjoint(rings: Rings, lmax: int, Q, U, nthreads: int = 0):
                                            _dp(gE.view(np.float64)), _dp(gB.view(np.float64)), nthreads)
     assert rc == 0
     return gE, gB
+
+
+def spin_analyze(rings: Rings, lmax: int, Q, U, ring_weight, niter: int = 0,
+                 nthreads: int = 0):
+    """Polarised analysis by the same quadrature rule as ``analyze`` (Eq.
+    sh-forward-quadrature for the spin-2 harmonics): (a_E, a_B) = h_m *
+    spin_adjoint(w Q, w U), h_0 = 1, h_m = 1/2, because the real-inner-product
+    transpose carries the factor 2 of the -m terms; then ``niter`` Jacobi
+    steps a <- a + A (f - Y a).  Returns (a_E, a_B), complex [nmaps, nalm]."""
+    Q = np.atleast_2d(np.asarray(Q, dtype=np.float64))
+    U = np.atleast_2d(np.asarray(U, dtype=np.float64))
+    w = np.repeat(np.asarray(ring_weight, dtype=np.float64), rings.J)
+    h = np.where(_m_of_index(lmax) == 0, 1.0, 0.5)
+
+    def quad(q, u):
+        gE, gB = spin_adjoint(rings, lmax, q * w, u * w, nthreads)
+        return gE * h, gB * h
+
+    aE, aB = quad(Q, U)
+    for _ in range(niter):
+        q, u = spin_synthesize(rings, lmax, aE, aB, nthreads)
+        dE, dB = quad(Q - q, U - u)
+        aE, aB = aE + dE, aB + dB
+    return aE, aB

@@ -583,3 +583,39 @@ def test_polarised_adjoint_is_explicit_transpose():
     m0 = np.array([m == 0 for m in range(lmax + 1) for _ in range(m, lmax + 1)])
     keep = np.concatenate([np.ones(n, bool), ~m0, np.ones(n, bool), ~m0])
     np.testing.assert_allclose(YT[:, keep], Y[:, keep], atol=1e-13)
+
+
+def test_polarised_analysis_exact_on_gauss_legendre_grid():
+    """On a Gauss-Legendre grid (L+1 rings, J = 2L+1) the quadrature is exact
+    for the spin-2 harmonics too: spin_analyze recovers band-limited a_E, a_B
+    (l >= 2; the l < 2 coefficients do not enter the maps and come back 0)."""
+    lmax = 12
+    rings, w = oracle.gauss_legendre_rings(lmax + 1, 2 * lmax + 1)
+    aE = _random_alm(lmax, 2, 71)
+    aB = _random_alm(lmax, 2, 72)
+    lcol = np.array([l for m in range(lmax + 1) for l in range(m, lmax + 1)])
+    aE[:, lcol < 2] = 0
+    aB[:, lcol < 2] = 0
+    Q, U = oracle.spin_synthesize(rings, lmax, aE, aB)
+    gE, gB = oracle.spin_analyze(rings, lmax, Q, U, 2 * math.pi * w / rings.J)
+    np.testing.assert_allclose(gE, aE, atol=5e-14)
+    np.testing.assert_allclose(gB, aB, atol=5e-14)
+
+
+def test_polarised_analysis_refinement_converges_on_healpix():
+    nside, lmax = 8, 16
+    rings = oracle.healpix_rings(nside)
+    w = np.full(rings.nrings, 4 * math.pi / rings.npix)
+    aE = _random_alm(lmax, 1, 73)
+    aB = _random_alm(lmax, 1, 74)
+    lcol = np.array([l for m in range(lmax + 1) for l in range(m, lmax + 1)])
+    aE[:, lcol < 2] = 0
+    aB[:, lcol < 2] = 0
+    Q, U = oracle.spin_synthesize(rings, lmax, aE, aB)
+    err = []
+    for k in (0, 2, 4, 8, 16):
+        gE, gB = oracle.spin_analyze(rings, lmax, Q, U, w, niter=k)
+        err.append(max(np.abs(gE - aE).max(), np.abs(gB - aB).max()))
+    assert err[0] > 1e-3
+    assert all(e1 < 0.2 * e0 for e0, e1 in zip(err[:-1], err[1:]) if e0 > 1e-13)
+    assert err[-1] < 1e-12
