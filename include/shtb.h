@@ -75,6 +75,12 @@ typedef struct {
                           the plan of this (nside, lmax, eps, options) from it if a
                           valid file is there, else builds the plan and writes the
                           file (a missing, unreadable or corrupt file is rebuilt)   */
+    int gpu_build;     /* 1: the plan builder runs the interpolative decompositions of
+                          each butterfly level as one batch on the plan's GPU (same
+                          algorithm and truncation rule as the host); 0: on the host */
+    int spin;          /* 0: scalar plan; 2: polarised (spin-2) plan, whose transforms
+                          are shtb_synthesize_spin (the spin-weighted transforms of
+                          Sec. 5, by compressing the spin-weighted operators)      */
 } shtb_plan_opts;
 
 /* Plan statistics (algorithmic counts; used for roofline accounting). */
@@ -102,6 +108,8 @@ typedef struct {
     long long n_ident;              /* identity entries of the interpolation matrices  */
     int depth_hist[16];             /* (m, parity) count per butterfly depth          */
     int from_cache;                 /* 1: the plan was read from a plan file          */
+    int spin;                       /* 0 scalar, 2 polarised; for a polarised plan the
+                                       element and byte counts cover both operators  */
 } shtb_plan_stats_t;
 
 /* Fill *opts with defaults.  Returns SHTB_EINVAL on NULL. */
@@ -127,13 +135,30 @@ int shtb_plan_opts_init(shtb_plan_opts *opts);
 int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts,
                      shtb_plan *out);
 
+/*
+ * Polarised plans (opts->spin = 2).  The spin-2 transform needs two real
+ * operators per m, F+ and F- = (2_lambda +- (-2)_lambda)/2, where
+ * sY_lm = s_lambda_lm(theta) e^{i m phi} (Newman-Penrose convention).  F+
+ * has the mirror parity (-1)^(l+m) of the scalar functions and F- the
+ * opposite one.  A polarised plan holds both, each compressed by the
+ * butterfly of Sec. 3.2 at tolerance eps.  With eps <= 0 both are stored
+ * uncompressed, as residual blocks at depth 0, which suits small sizes only.
+ * The paper's Sec. 5 offers two routes: a reduction to three scalar
+ * transforms, or compressing the spin-weighted operators.  This plan takes
+ * the second.  Polarised plans serve shtb_synthesize_spin,
+ * shtb_adjoint_spin and shtb_analyze_spin; the scalar calls and batches
+ * return SHTB_ENOTSUP on them.  Plan files and cache_dir hold both
+ * operators.
+ */
+
 /* Release a plan and all device memory it owns (NULL is accepted). */
 int shtb_plan_destroy(shtb_plan plan);
 
 /*
  * Plan files (the paper's precomputed-data files).  shtb_plan_save writes
  * the plan -- host tables and every device array, with a format version, the
- * plan's key (nside, lmax, eps, leaf_cols, max_depth, rho) and a checksum --
+ * plan's key (nside, lmax, eps, leaf_cols, max_depth, rho, spin) and a
+ * checksum; a polarised plan's file holds both of its operators --
  * to `path` (written to path.tmp, then renamed).  shtb_plan_load builds a
  * plan on opts->device (or the current device; other opts fields are taken
  * from the file) from such a file.  Errors: SHTB_EIO (cannot open, read or
@@ -175,6 +200,50 @@ int shtb_synthesize(shtb_plan plan, const double *alm_dev, double *map_dev, int 
  */
 int shtb_adjoint(shtb_plan plan, const double *map_dev, double *alm_dev, int nmaps,
                  void *stream);
+
+/*
+ * Polarised synthesis, HEALPix convention: (Q + iU) = -sum (aE + i aB) 2Y and
+ * (Q - iU) = -sum (aE - i aB) (-2)Y.  Per m and ring this is
+ * Q_m = -sum_l [aE F+ + i aB F-] and U_m = -sum_l [aB F+ - i aE F-], with
+ * Q = Re Q_0 + 2 sum_{m>=1} Re(Q_m e^{i m phi}), and the same for U.  Each
+ * operator is applied to the E and B coefficients of all pairs together
+ * (one read of its plan data per 8 inputs), then a combine pass and the
+ * ring stage of shtb_synthesize run.
+ * alm_dev: [npairs][2][nalm] complex128, E then B per pair; l < 2 terms
+ * contribute nothing, and Im a_l0 is ignored.
+ * map_dev: [npairs][2][12 nside^2] float64, Q then U.
+ * Errors: as shtb_synthesize; SHTB_ENOTSUP if the plan is not polarised.
+ */
+int shtb_synthesize_spin(shtb_plan plan, const double *alm_dev, double *map_dev, int npairs,
+                         void *stream);
+
+/*
+ * Transpose of shtb_synthesize_spin under real inner products over the
+ * (Re, Im) pairs of aE and aB (the convention of shtb_adjoint):
+ * <synthesize_spin(a), f> = <a, adjoint_spin(f)>.  The steps are the ring
+ * sums of the Q and U maps (forward FFT and unwrap, as in shtb_adjoint), the
+ * transposed combine (E: -G_Q for F+ and -i G_U for F-; B: -G_U for F+ and
+ * i G_Q for F-, folded by each operator's mirror parity), and the
+ * transposed butterflies of F+ and F-, whose outputs are summed, x2 for
+ * m >= 1.  The compressed plan's adjoint is the exact transpose of its
+ * synthesis.
+ * map_dev: [npairs][2][12 nside^2] (Q, U); alm_dev: [npairs][2][nalm]
+ * complex128 (E, B; written, Im a_l0 = 0).  Errors as shtb_synthesize_spin.
+ */
+int shtb_adjoint_spin(shtb_plan plan, const double *map_dev, double *alm_dev, int npairs,
+                      void *stream);
+
+/*
+ * Polarised analysis by the same ring quadrature as shtb_analyze (Eq.
+ * sh-forward-quadrature for the spin-2 harmonics, which are orthonormal
+ * like the scalar ones): (aE, aB) = h_m shtb_adjoint_spin(w Q, w U) with
+ * h_0 = 1 and h_m = 1/2, then niter Jacobi steps a += A (f - Y a).  Layouts
+ * are those of shtb_adjoint_spin; ring_weight_dev and niter are as for
+ * shtb_analyze.  Errors as shtb_synthesize_spin, plus SHTB_EINVAL for niter
+ * or aliasing as in shtb_analyze.
+ */
+int shtb_analyze_spin(shtb_plan plan, const double *map_dev, double *alm_dev, int npairs,
+                      const double *ring_weight_dev, int niter, void *stream);
 
 /*
  * Spherical-harmonic analysis by ring quadrature (Eq. sh-forward-quadrature):
@@ -388,6 +457,14 @@ int shtb_test_host_id(int rows, int n, const double *A, double eps, int *k_out, 
                       double *T_out);
 
 /*
+ * The same decomposition through the GPU plan builder's batched kernel, on
+ * the current device (A on the host; n <= 128).  Outputs as
+ * shtb_test_host_id.  Errors: SHTB_EINVAL, SHTB_ENOMEM, SHTB_ECUDA.
+ */
+int shtb_test_gpu_id(int rows, int n, const double *A, double eps, int *k_out, int *skel_out,
+                     double *T_out);
+
+/*
  * Host-only check of the butterfly compression (Sec. 3.2) of one Legendre
  * matrix Lambda^{m,t} (rows l = m+t+2j, columns the HEALPix rings with
  * z >= 0): builds the compressed operator exactly as shtb_plan_create does
@@ -399,6 +476,16 @@ int shtb_test_host_id(int rows, int n, const double *A, double eps, int *k_out, 
  */
 int shtb_test_host_butterfly(int nside, int lmax, double eps, int m, int t, int leaf_cols,
                              const double *a, double *q_out, double *q_exact, long long *info);
+
+/*
+ * Host-only check of the spin-weighted functions of spin plans (the
+ * polarised transform, Sec. 5): s_lambda_lm(z_r) for s = +2 or -2 and
+ * l = m..lmax at HEALPix half-ring r (0-based from the north pole), as the
+ * plan builder computes them (Wigner recurrence in l, Newman-Penrose
+ * convention: sY_lm = s_lambda_lm e^{i m phi}).  out: lmax - m + 1 doubles
+ * (host; 0 for l < 2).  Errors: SHTB_EINVAL.
+ */
+int shtb_test_host_spin_column(int nside, int lmax, int m, int s, int r, double *out);
 
 #ifdef __cplusplus
 }

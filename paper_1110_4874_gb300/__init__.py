@@ -44,7 +44,7 @@ class ShtbError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("leaf_cols", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("rho", ctypes.c_double), ("nthreads", ctypes.c_int), ("device", ctypes.c_int),
-                ("cache_dir", ctypes.c_char_p)]
+                ("cache_dir", ctypes.c_char_p), ("gpu_build", ctypes.c_int), ("spin", ctypes.c_int)]
 
 
 class PlanStats(ctypes.Structure):
@@ -57,7 +57,7 @@ class PlanStats(ctypes.Structure):
                 ("recurrence_flops", ctypes.c_double), ("phi_flops_per_map", ctypes.c_double),
                 ("build_seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
                 ("n_ident", ctypes.c_longlong), ("depth_hist", ctypes.c_int * 16),
-                ("from_cache", ctypes.c_int)]
+                ("from_cache", ctypes.c_int), ("spin", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "depth_hist"}
@@ -94,6 +94,9 @@ SIGNATURES = {
     "shtb_synthesize": (_I, [_P, _P, _P, _I, _P]),
     "shtb_adjoint": (_I, [_P, _P, _P, _I, _P]),
     "shtb_analyze": (_I, [_P, _P, _P, _I, _P, _I, _P]),
+    "shtb_synthesize_spin": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_adjoint_spin": (_I, [_P, _P, _P, _I, _P]),
+    "shtb_analyze_spin": (_I, [_P, _P, _P, _I, _P, _I, _P]),
     "shtb_synthesize_host": (_I, [_P, _P, _P, _I, _P]),
     "shtb_adjoint_host": (_I, [_P, _P, _P, _I, _P]),
     "shtb_strerror": (ctypes.c_char_p, [_I]),
@@ -118,8 +121,10 @@ SIGNATURES = {
     "shtb_batch_schedule": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "shtb_test_batch_stall": (_I, [_P, _I]),
     "shtb_test_host_id": (_I, [_I, _I, _DP, _D, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
+    "shtb_test_gpu_id": (_I, [_I, _I, _DP, _D, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP]),
     "shtb_test_host_butterfly": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
                                       ctypes.POINTER(ctypes.c_longlong)]),
+    "shtb_test_host_spin_column": (_I, [_I, _I, _I, _I, _I, _DP]),
 }
 
 _lib = None
@@ -192,8 +197,11 @@ def shtb_last_error_message() -> str:
 
 def shtb_plan_create(nside: int, lmax: int, eps: float = 0.0, leaf_cols: int = 32,
                      max_depth: int = -1, rho: float = 0.0, nthreads: int = 0,
-                     device: int = -1, cache_dir: str | None = None) -> ctypes.c_void_p:
+                     device: int = -1, cache_dir: str | None = None,
+                     spin: int = 0, gpu_build: bool = False) -> ctypes.c_void_p:
     opts = shtb_plan_opts_init()
+    opts.spin = spin
+    opts.gpu_build = 1 if gpu_build else 0
     opts.leaf_cols, opts.max_depth, opts.rho = leaf_cols, max_depth, rho
     opts.nthreads, opts.device = nthreads, device
     opts.cache_dir = os.fsencode(cache_dir) if cache_dir is not None else None
@@ -252,6 +260,31 @@ def shtb_synthesize_noalloc(plan, alm, maps, nmaps: int, stream=None) -> None:
 def shtb_adjoint(plan, maps, alm, nmaps: int, stream=None) -> None:
     import torch
     _call_dev("shtb_adjoint", plan, maps, torch.float64, alm, torch.complex128, nmaps, stream)
+
+
+def shtb_synthesize_spin(plan, alm, maps, npairs: int, stream=None) -> None:
+    """Polarised synthesis: alm complex128 [npairs][2][nalm] (E, B) -> maps
+    float64 [npairs][2][npix] (Q, U), on a plan created with spin=2."""
+    import torch
+    _call_dev("shtb_synthesize_spin", plan, alm, torch.complex128, maps, torch.float64, npairs, stream)
+
+
+def shtb_adjoint_spin(plan, maps, alm, npairs: int, stream=None) -> None:
+    """Transpose of shtb_synthesize_spin: maps float64 [npairs][2][npix]
+    (Q, U) -> alm complex128 [npairs][2][nalm] (E, B)."""
+    import torch
+    _call_dev("shtb_adjoint_spin", plan, maps, torch.float64, alm, torch.complex128, npairs, stream)
+
+
+def shtb_analyze_spin(plan, maps, alm, npairs: int, ring_weight=None, niter: int = 0,
+                      stream=None) -> None:
+    """Polarised quadrature analysis (+ niter Jacobi steps): maps [npairs][2][npix]
+    (Q, U) -> alm [npairs][2][nalm] (E, B); ring_weight as for shtb_analyze."""
+    import torch
+    w = None if ring_weight is None else _dptr(ring_weight, torch.float64, "ring_weight")
+    _check(lib().shtb_analyze_spin(plan, _dptr(maps, torch.float64, "maps"),
+                                   _dptr(alm, torch.complex128, "alm"), int(npairs), w, int(niter),
+                                   _stream_handle(stream)), "shtb_analyze_spin")
 
 
 def shtb_analyze(plan, maps, alm, nmaps: int, ring_weight=None, niter: int = 0,
@@ -357,6 +390,21 @@ def shtb_test_host_id(A, eps: float):
     return kk, skel[:kk].copy(), T[:kk * n].reshape(kk, n).copy()
 
 
+def shtb_test_gpu_id(A, eps: float):
+    """shtb_test_host_id through the GPU plan builder's kernel."""
+    import numpy as np
+    A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    rows, n = A.shape
+    k = ctypes.c_int()
+    skel = np.zeros(max(n, 1), dtype=np.int32)
+    T = np.zeros(max(n * n, 1))
+    _check(lib().shtb_test_gpu_id(rows, n, A.ctypes.data_as(_DP), float(eps), ctypes.byref(k),
+                                  skel.ctypes.data_as(ctypes.POINTER(_I)), T.ctypes.data_as(_DP)),
+           "shtb_test_gpu_id")
+    kk = k.value
+    return kk, skel[:kk].copy(), T[:kk * n].reshape(kk, n).copy()
+
+
 def shtb_test_host_butterfly(nside: int, lmax: int, eps: float, m: int, t: int, a,
                              leaf_cols: int = 32):
     """Compressed and dense Lambda^T a for one (m, parity) on the host."""
@@ -371,6 +419,15 @@ def shtb_test_host_butterfly(nside: int, lmax: int, eps: float, m: int, t: int, 
                                           qe.ctypes.data_as(_DP), info),
            "shtb_test_host_butterfly")
     return q, qe, {"depth": info[0], "n_dense": info[1], "n_r": info[2], "n_ident": info[3]}
+
+
+def shtb_test_host_spin_column(nside: int, lmax: int, m: int, s: int, r: int):
+    """s_lambda_lm (s = +-2) at half-ring r for l = m..lmax, as spin plans build it."""
+    import numpy as np
+    out = np.zeros(lmax - m + 1)
+    _check(lib().shtb_test_host_spin_column(nside, lmax, m, s, r, out.ctypes.data_as(_DP)),
+           "shtb_test_host_spin_column")
+    return out
 
 
 def shtb_batch_opts_init() -> BatchOpts:
@@ -481,6 +538,44 @@ class Plan:
         shtb_adjoint(self._h, f, out, nmaps, stream)
         return out[0] if squeeze else out
 
+    def synthesize_spin(self, alm, out=None, stream=None):
+        """Polarised synthesis on a spin=2 plan: alm complex128 [npairs, 2, nalm]
+        (or [2, nalm]), E then B -> maps float64 [npairs, 2, npix], Q then U."""
+        import torch
+        squeeze = alm.dim() == 2
+        a = alm.reshape(-1, 2, self.nalm).contiguous()
+        npairs = a.shape[0]
+        if out is None:
+            out = torch.empty((npairs, 2, self.npix), dtype=torch.float64, device=a.device)
+        shtb_synthesize_spin(self._h, a, out, npairs, stream)
+        return out[0] if squeeze else out
+
+    def adjoint_spin(self, maps, out=None, stream=None):
+        """Transpose of synthesize_spin: maps float64 [npairs, 2, npix] (or
+        [2, npix]), Q then U -> complex128 [npairs, 2, nalm], E then B."""
+        import torch
+        squeeze = maps.dim() == 2
+        f = maps.reshape(-1, 2, self.npix).contiguous()
+        npairs = f.shape[0]
+        if out is None:
+            out = torch.empty((npairs, 2, self.nalm), dtype=torch.complex128, device=f.device)
+        shtb_adjoint_spin(self._h, f, out, npairs, stream)
+        return out[0] if squeeze else out
+
+    def analyze_spin(self, maps, niter: int = 0, ring_weight=None, out=None, stream=None):
+        """Polarised analysis on a spin=2 plan: maps [npairs, 2, npix] (or [2,
+        npix]), Q then U -> complex128 [npairs, 2, nalm], E then B."""
+        import torch
+        squeeze = maps.dim() == 2
+        f = maps.reshape(-1, 2, self.npix).contiguous()
+        npairs = f.shape[0]
+        if ring_weight is not None and ring_weight.numel() != self.nrings:
+            raise ValueError(f"ring_weight needs one weight per ring ({self.nrings})")
+        if out is None:
+            out = torch.empty((npairs, 2, self.nalm), dtype=torch.complex128, device=f.device)
+        shtb_analyze_spin(self._h, f, out, npairs, ring_weight, niter, stream)
+        return out[0] if squeeze else out
+
     def analyze(self, maps, niter: int = 0, ring_weight=None, out=None, stream=None):
         """maps float64 [nmaps, npix] (or [npix]) -> a_lm complex128 by ring
         quadrature plus ``niter`` Jacobi refinement steps (shtb_analyze)."""
@@ -541,15 +636,38 @@ def _autograd_function():
             g = ctx.plan.adjoint(grad_maps.contiguous())
             return g, None
 
-    return Synthesis
+    class PolarisedSynthesis(torch.autograd.Function):
+        """(Q, U) = Y_pol (a_E, a_B) with shtb_adjoint_spin as its backward."""
+
+        @staticmethod
+        def forward(ctx, alm, plan):
+            ctx.plan = plan
+            return plan.synthesize_spin(alm)
+
+        @staticmethod
+        def backward(ctx, grad_maps):
+            return ctx.plan.adjoint_spin(grad_maps.contiguous()), None
+
+    return Synthesis, PolarisedSynthesis
 
 
 _synth_fn = None
+_spin_fn = None
 
 
 def synthesize(alm, plan: Plan):
     """Differentiable synthesis: maps = Y alm, backward through shtb_adjoint."""
-    global _synth_fn
+    global _synth_fn, _spin_fn
     if _synth_fn is None:
-        _synth_fn = _autograd_function()
+        _synth_fn, _spin_fn = _autograd_function()
     return _synth_fn.apply(alm, plan)
+
+
+def synthesize_spin(alm, plan: Plan):
+    """Differentiable polarised synthesis on a spin=2 plan: alm [npairs, 2,
+    nalm] (E, B) -> maps [npairs, 2, npix] (Q, U); backward through
+    shtb_adjoint_spin."""
+    global _synth_fn, _spin_fn
+    if _spin_fn is None:
+        _synth_fn, _spin_fn = _autograd_function()
+    return _spin_fn.apply(alm, plan)

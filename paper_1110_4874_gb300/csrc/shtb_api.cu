@@ -87,9 +87,17 @@ int ensure_ws(shtb_plan_s *p, int nmaps)
     return SHTB_OK;
 }
 
+int check_buffers(shtb_plan p, const void *a, const void *b, int nmaps);
+
 int check_call(shtb_plan p, const void *a, const void *b, int nmaps)
 {
     if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
+    if (p->kind != 0) return shtb_fail(SHTB_ENOTSUP, "a polarised plan serves shtb_synthesize_spin only");
+    return check_buffers(p, a, b, nmaps);
+}
+
+int check_buffers(shtb_plan p, const void *a, const void *b, int nmaps)
+{
     if (!a || !b) return shtb_fail(SHTB_EINVAL, "NULL buffer");
     if (nmaps < 1) return shtb_fail(SHTB_EINVAL, "nmaps must be >= 1");
     if (((uintptr_t)a & 15) || ((uintptr_t)b & 15))
@@ -223,8 +231,83 @@ int shtb_plan_opts_init(shtb_plan_opts *o)
     o->nthreads = 0;
     o->device = -1;
     o->cache_dir = nullptr;
+    o->gpu_build = 0;
+    o->spin = 0;
     return SHTB_OK;
 }
+
+namespace {
+
+void finish_stats(shtb_plan_s *p, std::chrono::steady_clock::time_point t0)
+{
+    p->opts.cache_dir = nullptr;          // the caller's string is not kept
+    p->stats.kernel_launches = 0;
+    p->stats.nside = p->nside;
+    p->stats.lmax = p->lmax;
+    p->stats.eps = p->eps;
+    p->stats.nrings = p->nrings;
+    p->stats.npix = p->npix;
+    p->stats.nalm = p->nalm;
+    if (!p->bf) {
+        p->stats.compressed = 0;
+        p->stats.depth_hist[0] = 2 * (p->lmax + 1);
+    }
+    p->stats.build_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// A fresh, empty plan for this key.  A polarised plan (opts.spin = 2) holds
+// the F+ operator (kind 1) and owns the F- one (kind 2) as its partner.
+shtb_plan_s *new_plan(const shtb_plan_opts &o, int nside, int lmax, double eps, int dev)
+{
+    auto make = [&](int kind) {
+        shtb_plan_s *p = new (std::nothrow) shtb_plan_s();
+        if (!p) return p;
+        p->opts = o;
+        p->nside = nside;
+        p->lmax = lmax;
+        p->eps = eps;
+        p->device = dev;
+        p->kind = kind;
+        return p;
+    };
+    shtb_plan_s *p = make(o.spin == 2 ? 1 : 0);
+    if (p && o.spin == 2) {
+        p->partner = make(2);
+        if (!p->partner) {
+            delete p;
+            return nullptr;
+        }
+        p->partner->opts.cache_dir = nullptr;
+    }
+    return p;
+}
+
+// Builds a fresh plan: ring tables and recurrence tables, and the butterfly
+// when eps > 0 or the operator is polarised (depth 0 only when eps <= 0).
+int build_plan(shtb_plan_s *p)
+{
+    int rc = shtb_build_dense_plan(p);
+    if (!rc && (p->eps > 0 || p->kind != 0)) rc = shtb_build_butterfly(p);
+    if (!rc && p->partner) rc = build_plan(p->partner);
+    return rc;
+}
+
+// A polarised plan reports both operators' element and byte counts.
+void combine_polarised_stats(shtb_plan_s *p)
+{
+    const shtb_plan_s *q = p->partner;
+    p->stats.spin = 2;
+    p->stats.compressed = p->eps > 0 ? 1 : 0;
+    p->stats.n_dense += q->stats.n_dense;
+    p->stats.n_rstored += q->stats.n_rstored;
+    p->stats.n_ident += q->stats.n_ident;
+    p->stats.plan_device_bytes += q->stats.plan_device_bytes;
+    p->stats.plan_read_bytes += q->stats.plan_read_bytes;
+    for (int d = 0; d < 16; ++d) p->stats.depth_hist[d] += q->stats.depth_hist[d];
+}
+
+}  // namespace
 
 int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts, shtb_plan *out)
 {
@@ -236,27 +319,18 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
     if (lmax > 8192) return shtb_fail(SHTB_ENOTSUP, "lmax > 8192");
     if (nside > 2048) return shtb_fail(SHTB_ENOTSUP, "nside > 2048");
     auto t0 = std::chrono::steady_clock::now();
-    shtb_plan_s *p = new (std::nothrow) shtb_plan_s();
-    if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
     shtb_plan_opts o;
     shtb_plan_opts_init(&o);
     if (opts) o = *opts;
-    p->opts = o;
-    p->nside = nside;
-    p->lmax = lmax;
-    p->eps = eps;
+    if (o.spin != 0 && o.spin != 2) return shtb_fail(SHTB_EINVAL, "spin must be 0 (scalar) or 2 (polarised)");
     int dev = o.device;
     if (dev < 0) {
-        if (cudaGetDevice(&dev) != cudaSuccess) {
-            delete p;
-            return shtb_fail(SHTB_ECUDA, "no CUDA device");
-        }
+        if (cudaGetDevice(&dev) != cudaSuccess) return shtb_fail(SHTB_ECUDA, "no CUDA device");
     } else if (cudaSetDevice(dev) != cudaSuccess) {
-        delete p;
         return shtb_fail(SHTB_ECUDA, "cudaSetDevice failed");
     }
-    p->device = dev;
-    int rc = SHTB_OK;
+    shtb_plan_s *p = new_plan(o, nside, lmax, eps, dev);
+    if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
     bool loaded = false;
     std::string cpath;
     if (o.cache_dir) {
@@ -264,44 +338,25 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
         if (plan_load(p, cpath.c_str()) == SHTB_OK) {
             loaded = true;
         } else {                          // missing or invalid file: start over and rebuild
-            shtb_plan_s *fresh = new (std::nothrow) shtb_plan_s();
-            if (!fresh) {
-                shtb_plan_destroy(p);
-                return shtb_fail(SHTB_ENOMEM, "plan struct");
-            }
-            fresh->opts = p->opts;
-            fresh->nside = nside;
-            fresh->lmax = lmax;
-            fresh->eps = eps;
-            fresh->device = dev;
             shtb_plan_destroy(p);
-            p = fresh;
+            p = new_plan(o, nside, lmax, eps, dev);
+            if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
         }
     }
     if (!loaded) {
-        rc = shtb_build_dense_plan(p);
-        if (rc == SHTB_OK && eps > 0.0) rc = shtb_build_butterfly(p);
+        const int rc = build_plan(p);
         if (rc) {
             shtb_plan_destroy(p);
             return rc;
         }
+        if (p->partner) {
+            finish_stats(p->partner, t0);
+            combine_polarised_stats(p);
+        }
         if (o.cache_dir) plan_save(p, cpath.c_str());   // a cache that cannot be written is only slower
     }
-    p->opts.cache_dir = nullptr;          // the caller's string is not kept
     p->stats.from_cache = loaded ? 1 : 0;
-    p->stats.kernel_launches = 0;
-    p->stats.nside = nside;
-    p->stats.lmax = lmax;
-    p->stats.eps = eps;
-    p->stats.nrings = p->nrings;
-    p->stats.npix = p->npix;
-    p->stats.nalm = p->nalm;
-    if (!p->bf) {
-        p->stats.compressed = 0;
-        p->stats.depth_hist[0] = 2 * (lmax + 1);
-    }
-    p->stats.build_seconds =
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    finish_stats(p, t0);
     *out = p;
     return SHTB_OK;
 }
@@ -335,15 +390,11 @@ int shtb_plan_load(const char *path, const shtb_plan_opts *opts, shtb_plan *out)
     } else {
         SHTB_CUDA_TRY(cudaSetDevice(dev));
     }
-    shtb_plan_s *p = new (std::nothrow) shtb_plan_s();
-    if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
     o.device = dev;
     o.cache_dir = nullptr;
-    p->opts = o;
-    p->nside = nside;
-    p->lmax = lmax;
-    p->eps = eps;
-    p->device = dev;
+    if (o.spin != 0 && o.spin != 2) return shtb_fail(SHTB_ECORRUPT, std::string("unknown spin in ") + path);
+    shtb_plan_s *p = new_plan(o, nside, lmax, eps, dev);
+    if (!p) return shtb_fail(SHTB_ENOMEM, "plan struct");
     if ((rc = plan_load(p, path))) {
         shtb_plan_destroy(p);
         return rc;
@@ -358,6 +409,7 @@ int shtb_plan_load(const char *path, const shtb_plan_opts *opts, shtb_plan *out)
 int shtb_plan_destroy(shtb_plan p)
 {
     if (!p) return SHTB_OK;
+    if (p->partner) shtb_plan_destroy(p->partner);
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->device) cudaSetDevice(p->device);
@@ -377,7 +429,7 @@ int shtb_plan_destroy(shtb_plan p)
 int shtb_plan_stats(shtb_plan p, shtb_plan_stats_t *out)
 {
     if (!p || !out) return shtb_fail(SHTB_EINVAL, "NULL argument");
-    p->stats.kernel_launches = p->launches;
+    p->stats.kernel_launches = p->launches + (p->partner ? p->partner->launches : 0);
     *out = p->stats;
     return SHTB_OK;
 }
@@ -403,32 +455,124 @@ int shtb_adjoint(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps,
     return run_adjoint(p, map_dev, (double2 *)alm_dev, nmaps, (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+int check_spin(shtb_plan p, const void *a, const void *b, int npairs, const char *what)
+{
+    if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
+    if (p->kind != 1 || !p->partner) return shtb_fail(SHTB_ENOTSUP, std::string(what) + " needs a polarised plan");
+    if (npairs < 1 || npairs > (1 << 20)) return shtb_fail(SHTB_EINVAL, "npairs must be in 1..2^20");
+    return check_buffers(p, a, b, 2 * npairs);
+}
+
+// E, B of every pair -> Q, U (2 npairs inputs and maps)
+int run_synthesis_spin(shtb_plan_s *p, const double2 *alm, double *map, int npairs, cudaStream_t st)
+{
+    const int nm = 2 * npairs;
+    shtb_plan_s *q = p->partner;
+    int rc;
+    if ((rc = ensure_ws(p, nm)) || (rc = ensure_ws(q, nm))) return rc;
+    Workspace wp = carve(p, nm), wq = carve(q, nm);
+    double *qt_plus = (double *)wp.adj, *qt_minus = (double *)wq.adj;   // parity halves, map-major
+    if ((rc = launch_bf_synth(p, alm, wp.ap, wp.bf, nullptr, nm, st, qt_plus))) return rc;
+    if ((rc = launch_bf_synth(q, alm, wq.ap, wq.bf, nullptr, nm, st, qt_minus))) return rc;
+    if ((rc = launch_spin_combine(p, qt_plus, qt_minus, wp.q, npairs, st))) return rc;
+    return launch_phi_synth(p, wp.q, map, nm, st);
+}
+
+// Q, U -> transposed E, B
+int run_adjoint_spin(shtb_plan_s *p, const double *map, double2 *alm, int npairs, cudaStream_t st)
+{
+    const int nm = 2 * npairs;
+    shtb_plan_s *q = p->partner;
+    int rc;
+    if ((rc = ensure_ws(p, nm)) || (rc = ensure_ws(q, nm))) return rc;
+    Workspace wp = carve(p, nm), wq = carve(q, nm);
+    double2 *g_plus = (double2 *)wp.adj, *g_minus = (double2 *)wq.adj;
+    if ((rc = launch_phi_adjoint(p, map, wp.q, nm, st))) return rc;      // ring sums of Q and U
+    if ((rc = launch_spin_uncombine(p, wp.q, g_plus, g_minus, npairs, st))) return rc;
+    if ((rc = launch_bf_adjoint(p, g_plus, wp.aacc, wp.bf, alm, nm, st))) return rc;
+    if ((rc = launch_bf_adjoint(q, g_minus, wq.aacc, wq.bf, wq.alm, nm, st))) return rc;
+    return launch_alm_add(p, alm, wq.alm, (size_t)nm * p->nalm, st);
+}
+
+// Quadrature analysis (Eq. sh-forward-quadrature) and Jacobi refinement over
+// nm stacked maps: a = h_m Y^T (w f), then a += h_m Y^T (w (f - Y a)).
+// synth/adjoint apply Y and Y^T; r (nm maps) and tmp (nm a_lm sets) are
+// workspace the two do not use.
+template <class Synth, class Adjoint>
+int run_analysis(shtb_plan_s *p, const double *map, double2 *alm, int nm, const double *ring_w, int niter,
+                 double *r, double2 *tmp, cudaStream_t st, Synth synth, Adjoint adjoint)
+{
+    const double w0 = 4.0 * 3.14159265358979323846 / (double)p->npix;   // equal-area HEALPix pixel weight
+    int rc;
+    if ((rc = launch_ring_weight(p, map, nullptr, ring_w, w0, r, nm, st))) return rc;
+    if ((rc = adjoint(r, alm))) return rc;
+    if ((rc = launch_alm_quadrature_add(p, alm, alm, nm, true, st))) return rc;
+    for (int it = 0; it < niter; ++it) {
+        if ((rc = synth(alm, r))) return rc;
+        if ((rc = launch_ring_weight(p, map, r, ring_w, w0, r, nm, st))) return rc;
+        if ((rc = adjoint(r, tmp))) return rc;
+        if ((rc = launch_alm_quadrature_add(p, tmp, alm, nm, false, st))) return rc;
+    }
+    return SHTB_OK;
+}
+
+int check_analysis_args(const void *map, const void *alm, int niter)
+{
+    if (niter < 0 || niter > SHTB_MAX_ANALYSIS_ITER)
+        return shtb_fail(SHTB_EINVAL, "niter must be in 0.." + std::to_string(SHTB_MAX_ANALYSIS_ITER));
+    if (map == alm) return shtb_fail(SHTB_EINVAL, "map and alm must not alias");
+    return SHTB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int shtb_synthesize_spin(shtb_plan p, const double *alm_dev, double *map_dev, int npairs, void *stream)
+{
+    int rc = check_spin(p, alm_dev, map_dev, npairs, "shtb_synthesize_spin");
+    if (rc) return rc;
+    return run_synthesis_spin(p, (const double2 *)alm_dev, map_dev, npairs, (cudaStream_t)stream);
+}
+
+int shtb_adjoint_spin(shtb_plan p, const double *map_dev, double *alm_dev, int npairs, void *stream)
+{
+    int rc = check_spin(p, map_dev, alm_dev, npairs, "shtb_adjoint_spin");
+    if (rc) return rc;
+    return run_adjoint_spin(p, map_dev, (double2 *)alm_dev, npairs, (cudaStream_t)stream);
+}
+
+int shtb_analyze_spin(shtb_plan p, const double *map_dev, double *alm_dev, int npairs,
+                      const double *ring_weight_dev, int niter, void *stream)
+{
+    int rc = check_spin(p, map_dev, alm_dev, npairs, "shtb_analyze_spin");
+    if (rc || (rc = check_analysis_args(map_dev, alm_dev, niter))) return rc;
+    const int nm = 2 * npairs;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_ws(p, nm)) || (rc = ensure_ws(p->partner, nm))) return rc;
+    Workspace w = carve(p, nm);   // w.map and w.alm: used by neither polarised transform
+    return run_analysis(
+        p, map_dev, (double2 *)alm_dev, nm, ring_weight_dev, niter, w.map, w.alm, st,
+        [&](const double2 *a, double *f) { return run_synthesis_spin(p, a, f, npairs, st); },
+        [&](const double *f, double2 *a) { return run_adjoint_spin(p, f, a, npairs, st); });
+}
+
 int shtb_analyze(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps,
                  const double *ring_weight_dev, int niter, void *stream)
 {
     int rc = check_call(p, map_dev, alm_dev, nmaps);
-    if (rc) return rc;
-    if (niter < 0 || niter > SHTB_MAX_ANALYSIS_ITER)
-        return shtb_fail(SHTB_EINVAL, "niter must be in 0.." + std::to_string(SHTB_MAX_ANALYSIS_ITER));
-    if ((const void *)map_dev == (const void *)alm_dev)
-        return shtb_fail(SHTB_EINVAL, "map and alm must not alias");
+    if (rc || (rc = check_analysis_args(map_dev, alm_dev, niter))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = ensure_ws(p, nmaps))) return rc;
     Workspace w = carve(p, nmaps);   // w.map: weighted residual, w.alm: adjoint of it
-    double2 *alm = (double2 *)alm_dev;
-    const double w0 = 4.0 * 3.14159265358979323846 / (double)p->npix;   // equal-area HEALPix pixel weight
-    // a = A f
-    if ((rc = launch_ring_weight(p, map_dev, nullptr, ring_weight_dev, w0, w.map, nmaps, st))) return rc;
-    if ((rc = run_adjoint(p, w.map, alm, nmaps, st))) return rc;
-    if ((rc = launch_alm_quadrature_add(p, alm, alm, nmaps, true, st))) return rc;
-    // Jacobi refinement: a += A (f - Y a)
-    for (int it = 0; it < niter; ++it) {
-        if ((rc = run_synthesis(p, alm, w.map, nmaps, st))) return rc;
-        if ((rc = launch_ring_weight(p, map_dev, w.map, ring_weight_dev, w0, w.map, nmaps, st))) return rc;
-        if ((rc = run_adjoint(p, w.map, w.alm, nmaps, st))) return rc;
-        if ((rc = launch_alm_quadrature_add(p, w.alm, alm, nmaps, false, st))) return rc;
-    }
-    return SHTB_OK;
+    return run_analysis(
+        p, map_dev, (double2 *)alm_dev, nmaps, ring_weight_dev, niter, w.map, w.alm, st,
+        [&](const double2 *a, double *f) { return run_synthesis(p, a, f, nmaps, st); },
+        [&](const double *f, double2 *a) { return run_adjoint(p, f, a, nmaps, st); });
 }
 
 int shtb_synthesize_host(shtb_plan p, const double *alm_host, double *map_host, int nmaps,

@@ -575,9 +575,9 @@ int shtb_batch_create(const shtb_request *reqs, int nreq, const shtb_batch_opts 
             delete b;
             return shtb_fail(SHTB_ENOTSUP, "batches serve synthesis requests (dir = 0) only");
         }
-        if (!r.plan->bf) {
+        if (!r.plan->bf || r.plan->kind != 0) {
             delete b;
-            return shtb_fail(SHTB_ENOTSUP, "batches need compressed plans (eps > 0)");
+            return shtb_fail(SHTB_ENOTSUP, "batches need compressed scalar plans (eps > 0)");
         }
         if (r.plan->device != dev) {
             delete b;

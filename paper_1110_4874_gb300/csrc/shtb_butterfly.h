@@ -23,11 +23,15 @@ struct IdResult {
 
 IdResult interp_decomp(const double *A, int rows, int n, int lda, double eps, double abs_floor);
 
+class GpuIdPool;
+
 struct BfParams {
     double eps = 1e-10;
     double abs_floor = 1e-30;        // the Appendix's negligible magnitude
     int leaf_cols = 32;
     int max_depth = -1;
+    GpuIdPool *gpu = nullptr;        // non-null: the IDs of each level run batched on the GPU
+    int slot = 0;                    // the calling thread's slot in that pool
 };
 
 // Residual block of one chain (local offsets).
@@ -62,7 +66,7 @@ struct BfChain {
     std::vector<std::pair<int, int>> top_rows;   // row intervals at the chosen depth
 };
 
-void compress_chain(const double *Lam, int n, int Z, const BfParams &prm, BfChain *out);
+int compress_chain(const double *Lam, int n, int Z, const BfParams &prm, BfChain *out);
 void apply_chain_host(const BfChain &ch, int Z, const double *a, double *q);
 
 }  // namespace shtb

@@ -97,6 +97,11 @@ struct BfPlanDev;
 struct shtb_plan_s {
     int nside = 0, lmax = 0;
     double eps = 0;
+    // operator: 0 the scalar Legendre functions; 1 and 2 the spin-2
+    // F+ and F- of a polarised plan (1 is the plan the caller holds, and it
+    // owns the F- plan as its partner)
+    int kind = 0;
+    shtb_plan_s *partner = nullptr;
     int device = 0;
     int nrings = 0, nhalf = 0;
     long long npix = 0, nalm = 0;
@@ -211,6 +216,16 @@ int launch_phi_synth_qt_ptr(const shtb_plan_s *p, const double *qt, int nb, doub
                             int b0, cudaStream_t st);
 
 // shtb_butterfly.cu
+// polarised synthesis (shtb_spin.cu): parity halves of F+ and F- (map-major,
+// inputs E, B per pair) -> ring-major Q_m, U_m spectra
+int launch_spin_combine(const shtb_plan_s *p, const double *qt_plus, const double *qt_minus, double2 *qring,
+                        int npairs, cudaStream_t st);
+// ... and its transpose: ring sums of Q, U -> entry-major parity gradients of
+// the F+ and F- butterflies; alm += add over n complex entries
+int launch_spin_uncombine(const shtb_plan_s *p, const double2 *G, double2 *g_plus, double2 *g_minus, int npairs,
+                          cudaStream_t st);
+int launch_alm_add(const shtb_plan_s *p, double2 *alm, const double2 *add, size_t n, cudaStream_t st);
+
 // analysis (shtb_analysis.cu): quadrature weighting of a map or a residual,
 // and alm += h_m g with h_0 = 1, h_m = 1/2
 int launch_ring_weight(const shtb_plan_s *p, const double *f, const double *y, const double *ring_w,

@@ -56,6 +56,7 @@ extern "C" int shtb_synthesize_noalloc(shtb_plan p, const double *alm_dev, doubl
                                        int nmaps, void *stream)
 {
     if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
+    if (p->kind != 0) return shtb_fail(SHTB_ENOTSUP, "a polarised plan serves shtb_synthesize_spin only");
     if (!alm_dev || !map_dev) return shtb_fail(SHTB_EINVAL, "NULL buffer");
     if (nmaps < 1) return shtb_fail(SHTB_EINVAL, "nmaps must be >= 1");
     if (((uintptr_t)alm_dev & 15) || ((uintptr_t)map_dev & 15))

@@ -22,13 +22,14 @@
 namespace {
 
 constexpr char kMagic[8] = {'S', 'H', 'T', 'B', 'P', 'L', 'A', 'N'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 struct Header {
     char magic[8];
     uint32_t version;
     uint32_t header_bytes;
     int32_t nside, lmax, leaf_cols, max_depth;
+    int32_t spin, reserved;          // 0 scalar, 2 polarised (two plan payloads: F+ then F-)
     double eps, rho;
     uint64_t payload_bytes;
     uint64_t checksum;
@@ -117,29 +118,13 @@ std::vector<const void **> pointer_fields(shtb_plan_s *p)
 bool key_matches(const Header &h, const shtb_plan_s *p)
 {
     return h.nside == p->nside && h.lmax == p->lmax && h.eps == p->eps && h.leaf_cols == p->opts.leaf_cols &&
-           h.max_depth == p->opts.max_depth && h.rho == p->opts.rho;
+           h.max_depth == p->opts.max_depth && h.rho == p->opts.rho && h.spin == p->opts.spin;
 }
 
-}  // namespace
-
-int plan_save(shtb_plan_s *p, const char *path)
+// one plan's payload: scalars, host vectors, device arrays, pointer indices
+bool write_payload(Writer &w, shtb_plan_s *p)
 {
-    const std::string tmp = std::string(path) + ".tmp";
-    FILE *f = fopen(tmp.c_str(), "wb");
-    if (!f) return shtb_fail(SHTB_EIO, std::string("cannot create plan file ") + tmp);
-    Header h{};
-    memcpy(h.magic, kMagic, 8);
-    h.version = kVersion;
-    h.header_bytes = sizeof(Header);
-    h.nside = p->nside;
-    h.lmax = p->lmax;
-    h.leaf_cols = p->opts.leaf_cols;
-    h.max_depth = p->opts.max_depth;
-    h.eps = p->eps;
-    h.rho = p->opts.rho;
-    bool ok = fwrite(&h, sizeof h, 1, f) == 1;          // rewritten with the sizes at the end
-    Writer w{f};
-    w.val(p->nrings); w.val(p->nhalf); w.val(p->npix); w.val(p->nalm);
+    w.val(p->nrings); w.val(p->nhalf); w.val(p->npix); w.val(p->nalm); w.val(p->kind);
     w.val(p->max_K_direct); w.val(p->max_M_mx); w.val(p->max_K_big); w.val(p->max_K_pow2); w.val(p->max_M_blue);
     w.val(p->blue_split); w.val(p->max_M_small);
     w.val(p->chunk_kind); w.val(p->chunk_pix); w.val(p->stats);
@@ -162,11 +147,7 @@ int plan_save(shtb_plan_s *p, const char *path)
         const uint64_t n = p->alloc_bytes[i];
         w.val(n);
         buf.resize(n);
-        if (cudaMemcpy(buf.data(), p->allocations[i], n, cudaMemcpyDeviceToHost) != cudaSuccess) {
-            fclose(f);
-            remove(tmp.c_str());
-            return shtb_fail(SHTB_ECUDA, "plan save: device copy failed");
-        }
+        if (cudaMemcpy(buf.data(), p->allocations[i], n, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
         w.raw(buf.data(), n);
     }
     // the plan's device pointers as allocation indices (0 = null)
@@ -176,43 +157,22 @@ int plan_save(shtb_plan_s *p, const char *path)
             if (p->allocations[i] == *fp) idx = i + 1;
         w.val(idx);
     }
-    h.payload_bytes = w.bytes;
-    h.checksum = w.sum.h;
-    ok = ok && w.ok && fseek(f, 0, SEEK_SET) == 0 && fwrite(&h, sizeof h, 1, f) == 1;
-    ok = (fclose(f) == 0) && ok;
-    if (!ok || rename(tmp.c_str(), path) != 0) {
-        remove(tmp.c_str());
-        return shtb_fail(SHTB_EIO, std::string("cannot write plan file ") + path);
-    }
-    return SHTB_OK;
+    return true;
 }
 
-// Fills a fresh plan (device, opts and key already set) from a file.
-int plan_load(shtb_plan_s *p, const char *path)
+// Fills p (device, opts and key already set) from one payload; returns
+// SHTB_OK with r.ok telling whether the bytes were well formed, or an
+// allocation error.
+int read_payload(Reader &r, shtb_plan_s *p, FILE *f)
 {
-    FILE *f = fopen(path, "rb");
-    if (!f) return shtb_fail(SHTB_EIO, std::string("cannot open plan file ") + path);
-    Header h{};
-    if (fread(&h, sizeof h, 1, f) != 1) {
-        fclose(f);
-        return shtb_fail(SHTB_ECORRUPT, std::string("plan file too short: ") + path);
-    }
-    if (memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion || h.header_bytes != sizeof(Header)) {
-        fclose(f);
-        return shtb_fail(SHTB_ECORRUPT, std::string("not a plan file of this version: ") + path);
-    }
-    if (!key_matches(h, p)) {
-        fclose(f);
-        return shtb_fail(SHTB_ECORRUPT, std::string("plan file is for another (nside, lmax, eps, options): ") + path);
-    }
-    Reader r{f};
-    r.limit = h.payload_bytes;
     const uint64_t big = 1ULL << 40;
-    r.val(p->nrings); r.val(p->nhalf); r.val(p->npix); r.val(p->nalm);
+    int kind = -1;
+    r.val(p->nrings); r.val(p->nhalf); r.val(p->npix); r.val(p->nalm); r.val(kind);
+    if (r.ok && kind != p->kind) r.ok = false;
     r.val(p->max_K_direct); r.val(p->max_M_mx); r.val(p->max_K_big); r.val(p->max_K_pow2); r.val(p->max_M_blue);
     r.val(p->blue_split); r.val(p->max_M_small);
     r.val(p->chunk_kind); r.val(p->chunk_pix);
-    shtb_plan_stats_t st{};
+    shtb_plan_stats_t st{};          // set once the uploads (which count their bytes) are done
     r.val(st);
     r.vec(p->ring_J, big); r.vec(p->ring_s, big); r.vec(p->ring_M, big); r.vec(p->ring_start, big);
     r.vec(p->direct_rings, big); r.vec(p->blue_rings, big); r.vec(p->big_rings, big);
@@ -246,7 +206,7 @@ int plan_load(shtb_plan_s *p, const char *path)
         if (!r.ok) break;
         void *d = nullptr;
         const int rc = plan_alloc_upload(p, &d, buf.data(), n);
-        if (rc) { fclose(f); return rc; }
+        if (rc) return rc;
     }
     for (const void **fp : pointer_fields(p)) {
         uint64_t idx = 0;
@@ -254,19 +214,88 @@ int plan_load(shtb_plan_s *p, const char *path)
         if (!r.ok || idx > p->allocations.size()) { r.ok = false; break; }
         *fp = idx ? p->allocations[idx - 1] : nullptr;
     }
+    p->stats = st;
+    (void)f;
+    return SHTB_OK;
+}
+
+}  // namespace
+
+int plan_save(shtb_plan_s *p, const char *path)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return shtb_fail(SHTB_EIO, std::string("cannot create plan file ") + tmp);
+    Header h{};
+    memcpy(h.magic, kMagic, 8);
+    h.version = kVersion;
+    h.header_bytes = sizeof(Header);
+    h.nside = p->nside;
+    h.lmax = p->lmax;
+    h.leaf_cols = p->opts.leaf_cols;
+    h.max_depth = p->opts.max_depth;
+    h.spin = p->opts.spin;
+    h.eps = p->eps;
+    h.rho = p->opts.rho;
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1;          // rewritten with the sizes at the end
+    Writer w{f};
+    bool dev_ok = write_payload(w, p);
+    if (dev_ok && p->partner) dev_ok = write_payload(w, p->partner);
+    if (!dev_ok) {
+        fclose(f);
+        remove(tmp.c_str());
+        return shtb_fail(SHTB_ECUDA, "plan save: device copy failed");
+    }
+    h.payload_bytes = w.bytes;
+    h.checksum = w.sum.h;
+    ok = ok && w.ok && fseek(f, 0, SEEK_SET) == 0 && fwrite(&h, sizeof h, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return shtb_fail(SHTB_EIO, std::string("cannot write plan file ") + path);
+    }
+    return SHTB_OK;
+}
+
+// Fills a fresh plan (device, opts and key already set; for a polarised key,
+// kind 1 with a fresh kind-2 partner) from a file.
+int plan_load(shtb_plan_s *p, const char *path)
+{
+    FILE *f = fopen(path, "rb");
+    if (!f) return shtb_fail(SHTB_EIO, std::string("cannot open plan file ") + path);
+    Header h{};
+    if (fread(&h, sizeof h, 1, f) != 1) {
+        fclose(f);
+        return shtb_fail(SHTB_ECORRUPT, std::string("plan file too short: ") + path);
+    }
+    if (memcmp(h.magic, kMagic, 8) != 0 || h.version != kVersion || h.header_bytes != sizeof(Header)) {
+        fclose(f);
+        return shtb_fail(SHTB_ECORRUPT, std::string("not a plan file of this version: ") + path);
+    }
+    if (!key_matches(h, p) || (h.spin == 2) != (p->partner != nullptr)) {
+        fclose(f);
+        return shtb_fail(SHTB_ECORRUPT, std::string("plan file is for another (nside, lmax, eps, options): ") + path);
+    }
+    Reader r{f};
+    r.limit = h.payload_bytes;
+    int rc = read_payload(r, p, f);
+    if (!rc && r.ok && p->partner) rc = read_payload(r, p->partner, f);
+    if (rc) {
+        fclose(f);
+        return rc;
+    }
     const bool complete = r.ok && r.bytes == h.payload_bytes && fgetc(f) == EOF;
     fclose(f);
     if (!complete || r.sum.h != h.checksum)
         return shtb_fail(SHTB_ECORRUPT, std::string("plan file failed its size or checksum check: ") + path);
-    p->stats = st;
     return SHTB_OK;
 }
 
 std::string plan_cache_path(const shtb_plan_s *p, const char *dir)
 {
     char name[256];
-    snprintf(name, sizeof name, "shtb_plan_v%u_n%d_l%d_e%a_lc%d_md%d_r%a.bin", kVersion, p->nside, p->lmax, p->eps,
-             p->opts.leaf_cols, p->opts.max_depth, p->opts.rho);
+    snprintf(name, sizeof name, "shtb_plan_v%u_n%d_l%d_e%a_lc%d_md%d_r%a_s%d.bin", kVersion, p->nside, p->lmax,
+             p->eps, p->opts.leaf_cols, p->opts.max_depth, p->opts.rho, p->opts.spin);
     std::string s(dir);
     if (!s.empty() && s.back() != '/') s += '/';
     return s + name;
@@ -287,5 +316,6 @@ int plan_read_key(const char *path, int *nside, int *lmax, double *eps, shtb_pla
     opts->leaf_cols = h.leaf_cols;
     opts->max_depth = h.max_depth;
     opts->rho = h.rho;
+    opts->spin = h.spin;
     return SHTB_OK;
 }

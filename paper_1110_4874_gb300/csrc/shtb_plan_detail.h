@@ -38,6 +38,10 @@ DD dd_pow(DD x, int m, int *E);
 void legendre_column(int L, int m, const HalfRing &h, DD cm, const std::vector<double> &b,
                      double *out);
 
+// Spin-weighted s_lambda_lm (s = +-2) at one half-ring for l = m..L (zero
+// below l = 2), by the Wigner recurrence in l; out has L - m + 1 slots.
+void spin_column(int L, int m, int s, const HalfRing &h, DD cm, double *out);
+
 constexpr double kCrop = 1e-30;   // Appendix: values below 1e-30 are neglected
 
 template <class F>

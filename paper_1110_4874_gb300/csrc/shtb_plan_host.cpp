@@ -140,6 +140,74 @@ void legendre_column(int L, int m, const HalfRing &h, DD cm, const std::vector<d
     }
 }
 
+// Spin-weighted s_lambda_lm (s = +-2) at one half-ring for l = m..L: the
+// Wigner three-term recurrence in l for d^l_{m,-s} on the normalised
+// functions s_lambda = (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}:
+//   l sqrt(((l+1)^2-m^2)((l+1)^2-s^2)) d^{l+1}
+//     = (2l+1)(l(l+1) z + m s) d^l - (l+1) sqrt((l^2-m^2)(l^2-s^2)) d^{l-1},
+// from l0 = max(m, 2).  Start values: for m >= 2, s_lambda_mm =
+// Ptilde_m^m sqrt(m(m-1)/((m+1)(m+2))) tan(theta/2)^s (the closed form
+// of d^m_{m,-s}, since sin^m = 2^m sin^m(theta/2) cos^m(theta/2)); for
+// m = 0, 1 the l = 2 closed forms.  The same power-of-two exponent
+// bookkeeping and 1e-30 crop as the scalar column.
+void spin_column(int L, int m, int s, const HalfRing &h, DD cm, double *out)
+{
+    for (int l = m; l <= L; ++l) out[l - m] = 0.0;
+    const int l0 = std::max(m, 2);
+    if (l0 > L) return;
+    const double z = h.z, st = to_double(h.sdd);
+    const bool near_pole = h.z > 0.5;
+    auto zmul = [&](double v) { return near_pole ? v - h.eps1 * v : z * v; };
+    const double tan_half = st / (1.0 + z);            // tan(theta/2), z >= 0
+    int E = 0;
+    double V0;
+    if (m >= 2) {
+        DD pm = dd_pow(h.sdd, m, &E) * cm;             // |Ptilde_m^m| = c_m sin^m
+        double v = to_double(pm) * std::sqrt((double)m * (m - 1) / ((double)(m + 1) * (m + 2)));
+        v *= s > 0 ? tan_half * tan_half : 1.0 / (tan_half * tan_half);
+        V0 = (m & 1) ? -v : v;                         // Condon-Shortley phase of Ptilde_m^m
+    } else {
+        const double c5 = std::sqrt(5.0 / (4.0 * shtb::kPiHi));
+        const double sh = std::sqrt(0.5 * h.eps1), ch = std::sqrt(0.5 * (1.0 + z));   // half angles
+        if (m == 0) V0 = c5 * std::sqrt(6.0) * sh * sh * ch * ch;
+        else if (s > 0) V0 = -c5 * 2.0 * sh * sh * sh * ch;
+        else V0 = c5 * 2.0 * sh * ch * ch * ch;
+    }
+    auto emit = [&](int l, double v) {
+        const double x = E == 0 ? v : std::ldexp(v, E);
+        out[l - m] = std::fabs(x) >= kCrop ? x : 0.0;
+    };
+    emit(l0, V0);
+    double Vp = 0.0, V = V0;
+    const double mm = (double)m * m, ss = (double)s * s;
+    for (int l = l0; l < L; ++l) {
+        const double dl = l;
+        const double den = dl * std::sqrt(((dl + 1) * (dl + 1) - mm) * ((dl + 1) * (dl + 1) - ss));
+        const double nrm = std::sqrt((2 * dl + 3) / (2 * dl + 1));
+        const double a = nrm * (2 * dl + 1) / den;
+        const double bcoef = l == l0 ? 0.0
+                                     : nrm * (dl + 1) * std::sqrt((dl * dl - mm) * (dl * dl - ss)) *
+                                           std::sqrt((2 * dl + 1) / (2 * dl - 1)) / den;
+        const double Vn = a * (dl * (dl + 1) * zmul(V) + (double)m * s * V) - bcoef * Vp;
+        Vp = V;
+        V = Vn;
+        if (E != 0 && V != 0.0) {
+            int k;
+            std::frexp(V, &k);
+            if (k + E > -900) {
+                Vp = std::ldexp(Vp, E);
+                V = std::ldexp(V, E);
+                E = 0;
+            } else if (k > 600) {
+                Vp = std::ldexp(Vp, -512);
+                V = std::ldexp(V, -512);
+                E += 512;
+            }
+        }
+        emit(l + 1, V);
+    }
+}
+
 }  // namespace shtb
 
 using shtb::diag_norms;
@@ -813,5 +881,17 @@ extern "C" int shtb_test_host_recurrence(int nside, int lmax, int m, int r, doub
             cur = nxt;
         }
     }
+    return SHTB_OK;
+}
+
+// s_lambda_lm (s = +-2) at half-ring r (0-based from the north pole) for
+// l = m..lmax, as the plan builder of spin plans computes it.
+extern "C" int shtb_test_host_spin_column(int nside, int lmax, int m, int s, int r, double *out)
+{
+    if (nside < 1 || lmax < 0 || m < 0 || m > lmax || (s != 2 && s != -2) || r < 0 || r >= 2 * nside || !out)
+        return shtb_fail(SHTB_EINVAL, "bad arguments");
+    const HalfRing h = half_ring(nside, r + 1);
+    const std::vector<DD> cm = diag_norms(lmax);
+    shtb::spin_column(lmax, m, s, h, cm[m], out);
     return SHTB_OK;
 }

@@ -98,3 +98,31 @@ def test_foreign_file_under_this_name_and_missing_file(tmp_path):
     assert e.value.code == sh.SHTB_EIO
     for p in (a, b, c):
         p.close()
+
+
+def test_polarised_plan_files(tmp_path):
+    """A polarised plan's file holds both operators: the loaded plan
+    synthesizes bit-identical Q/U maps; the cache directory keys on spin."""
+    d = str(tmp_path)
+    plan = sh.Plan(16, 32, 1e-10, spin=2, cache_dir=d)
+    assert plan.stats()["from_cache"] == 0 and plan.stats()["spin"] == 2
+    eb = np.stack([synthetic.gaussian_alm(32, 2, seed=5), synthetic.gaussian_alm(32, 2, seed=6)], axis=1)
+    a = torch.from_numpy(np.ascontiguousarray(eb)).cuda()
+    want = plan.synthesize_spin(a)
+    again = sh.Plan(16, 32, 1e-10, spin=2, cache_dir=d)
+    st0, st1 = plan.stats(), again.stats()
+    assert st1["from_cache"] == 1 and st1["spin"] == 2
+    for k in ("n_dense", "n_rstored", "n_ident", "plan_device_bytes"):
+        assert st0[k] == st1[k], k
+    assert torch.equal(again.synthesize_spin(a), want)
+    f = torch.from_numpy(np.random.default_rng(7).standard_normal((2, 2, plan.npix))).cuda()
+    assert torch.equal(again.adjoint_spin(f), plan.adjoint_spin(f))
+    scalar = sh.Plan(16, 32, 1e-10, cache_dir=d)          # same key but spin: its own file
+    assert scalar.stats()["from_cache"] == 0 and len(os.listdir(d)) == 2
+    path = str(tmp_path / "pol.bin")
+    plan.save(path)
+    back = sh.Plan.load(path)
+    assert back.stats()["spin"] == 2
+    assert torch.equal(back.synthesize_spin(a), want)
+    for p in (plan, again, scalar, back):
+        p.close()
