@@ -212,7 +212,7 @@ def run_ours(args, rank, world, dist):
     t0 = time.perf_counter()
     eps_plan = args.eps
     try:
-        plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols)
+        plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols, gpu_build=not args.host_build)
     except sh.ShtbError as e:
         if e.code != sh.SHTB_ENOTSUP or eps_plan <= 0:
             raise
@@ -344,7 +344,7 @@ def run_ours(args, rank, world, dist):
         "details": {"adjoint_ms_per_map": round(ms_adj, 4), "plain_ms_per_map": round(ms_plain, 4),
                     "batched_over_plain": round(ms_plain / value, 3),
                     "stage_ms_per_step": {k: round(v / max(ncalls, 1), 3) for k, v in stages.items() if v},
-                    "plan_build_s": round(plan_s, 2),
+                    "plan_build_s": round(plan_s, 2), "plan_built_on": "host" if args.host_build else "gpu",
                     "plan_device_gb": round(st["plan_device_bytes"] / 1e9, 3),
                     "n_recurrence": st["n_recurrence"], "n_dense": st["n_dense"],
                     "n_rstored": st["n_rstored"], "n_ident": st["n_ident"],
@@ -361,6 +361,7 @@ def run_ours(args, rank, world, dist):
         out["details"]["differentiation"] = differentiation(sh, synthetic, dev, plan_c4)
         plan_c4.close()
         out["details"]["polarised"] = polarised_synthesis(sh, synthetic, dev)
+        out["details"]["plan_build"] = plan_build_compare(sh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, cores, sample = oracle_sample(N, L, 1, args.cpu_rings, seed=2000)
         out["cpu_baseline"] = {"value": round(ms_cpu, 1), "unit": UNIT, "cores": cores,
@@ -498,6 +499,19 @@ def polarised_synthesis(sh, synthetic, dev, reps=5):
             "n_dense": st["n_dense"], "n_rstored": st["n_rstored"]}
 
 
+def plan_build_compare(sh, N=512, L=1024, eps=1e-10):
+    """Plan build time at Nside=512, L=1024: the IDs on the host cores vs
+    batched on the GPU (the same plan up to pivoting near-ties)."""
+    out = {"nside": N, "lmax": L, "eps": eps}
+    for name, gb in (("host_s", False), ("gpu_s", True)):
+        t0 = time.perf_counter()
+        p = sh.Plan(N, L, eps, gpu_build=gb)
+        out[name] = round(time.perf_counter() - t0, 2)
+        out["n_dense_" + name[:-2]] = p.stats()["n_dense"]
+        p.close()
+    return out
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: each step a bounded ring sample."""
     vals = []
@@ -538,6 +552,8 @@ def main():
     ap.add_argument("--cpu-rings", type=int, default=64, help="ring sample of the CPU baseline")
     ap.add_argument("--ref-rings", type=int, default=16, help="ring sample per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-build", action="store_true",
+                    help="build the plan's interpolative decompositions on the host, not the GPU")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the batched-serving and differentiation measurements")
     args = ap.parse_args()

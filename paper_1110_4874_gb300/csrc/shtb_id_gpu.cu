@@ -244,6 +244,14 @@ void gpu_id_pool_destroy(GpuIdPool *pool)
     delete pool;
 }
 
+double *gpu_id_staging(GpuIdPool *pool, int slot, long long nelem)
+{
+    if (cudaSetDevice(pool->device) != cudaSuccess) return nullptr;
+    GpuIdSlot &s = pool->slots[slot];
+    if (!grow(s.h_data, s.d_data, s.cap_data, std::max(1LL, nelem))) return nullptr;
+    return s.h_data;
+}
+
 int gpu_id_run(GpuIdPool *pool, int slot, const double *data, long long nelem, const std::vector<IdBlock> &blocks,
                double eps, double abs_floor, std::vector<IdResult> &out)
 {
@@ -263,7 +271,8 @@ int gpu_id_run(GpuIdPool *pool, int slot, const double *data, long long nelem, c
     for (const auto &b : blocks) nint += b.nc;
     if (!grow(s.h_int, s.d_int, cap_i, nint)) return shtb_fail(SHTB_ENOMEM, "plan build: id outputs");
     s.cap_int = (int)cap_i;
-    if (!grow(s.h_data, s.d_data, s.cap_data, std::max(1LL, nelem))) return shtb_fail(SHTB_ENOMEM, "plan build: id data");
+    if (data != s.h_data && !grow(s.h_data, s.d_data, s.cap_data, std::max(1LL, nelem)))
+        return shtb_fail(SHTB_ENOMEM, "plan build: id data");
     if (!grow(s.h_x, s.d_x, s.cap_x, (long long)nb * kXPer)) return shtb_fail(SHTB_ENOMEM, "plan build: id X");
     int col_off = 2 * nb, max_rows = 1;
     for (int i = 0; i < nb; ++i) {
@@ -276,7 +285,7 @@ int gpu_id_run(GpuIdPool *pool, int slot, const double *data, long long nelem, c
     }
     const size_t smem = sizeof(double) * (size_t)max_rows;
     if (smem > 160 * 1024) return shtb_fail(SHTB_ENOTSUP, "plan build: id block too tall for the GPU builder");
-    std::copy(data, data + nelem, s.h_data);
+    if (data != s.h_data) std::copy(data, data + nelem, s.h_data);
     SHTB_CUDA_TRY(cudaMemcpyAsync(s.d_data, s.h_data, sizeof(double) * nelem, cudaMemcpyHostToDevice, s.st));
     SHTB_CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, sizeof(IdDesc) * nb, cudaMemcpyHostToDevice, s.st));
     static std::once_flag attr;

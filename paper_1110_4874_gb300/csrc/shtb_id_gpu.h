@@ -23,6 +23,11 @@ class GpuIdPool;   // per-thread device buffers and streams
 GpuIdPool *gpu_id_pool_create(int device, int nthreads);
 void gpu_id_pool_destroy(GpuIdPool *pool);
 
+// A pinned host buffer of at least nelem doubles owned by the caller's slot,
+// for gathering the blocks straight into (gpu_id_run then copies nothing on
+// the host); nullptr on allocation failure.  Valid until the slot's next call.
+double *gpu_id_staging(GpuIdPool *pool, int slot, long long nelem);
+
 // IDs of every block of `data` (host memory, the blocks' elements), into
 // out[i] exactly as interp_decomp(data + blocks[i].off, rows, nc, rows, eps,
 // abs_floor) defines them (up to the order of floating-point sums).

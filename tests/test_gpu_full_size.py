@@ -55,7 +55,8 @@ def test_nside512_one_and_sixteen_maps(eps):
 
 @pytest.fixture(scope="module")
 def planck_plan():
-    plan = sh.Plan(2048, 4096, 1e-10)
+    # built by the GPU plan builder, as bench.py builds it
+    plan = sh.Plan(2048, 4096, 1e-10, gpu_build=True)
     yield plan
     plan.close()
 
