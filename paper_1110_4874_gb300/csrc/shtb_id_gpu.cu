@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 #include <vector>
 
 #include "shtb_id_gpu.h"
@@ -288,10 +287,8 @@ int gpu_id_run(GpuIdPool *pool, int slot, const double *data, long long nelem, c
     if (data != s.h_data) std::copy(data, data + nelem, s.h_data);
     SHTB_CUDA_TRY(cudaMemcpyAsync(s.d_data, s.h_data, sizeof(double) * nelem, cudaMemcpyHostToDevice, s.st));
     SHTB_CUDA_TRY(cudaMemcpyAsync(s.d_desc, s.h_desc, sizeof(IdDesc) * nb, cudaMemcpyHostToDevice, s.st));
-    static std::once_flag attr;
-    std::call_once(attr, [] {
-        cudaFuncSetAttribute(id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    });
+    if (smem > 48 * 1024)
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(id_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     id_kernel<<<nb, kIdThreads, smem, s.st>>>(s.d_data, s.d_desc, eps, abs_floor, s.d_int, s.d_int + nb,
                                               s.d_int, s.d_x);
     SHTB_CUDA_TRY(cudaGetLastError());

@@ -163,7 +163,7 @@ bool write_payload(Writer &w, shtb_plan_s *p)
 // Fills p (device, opts and key already set) from one payload; returns
 // SHTB_OK with r.ok telling whether the bytes were well formed, or an
 // allocation error.
-int read_payload(Reader &r, shtb_plan_s *p, FILE *f)
+int read_payload(Reader &r, shtb_plan_s *p)
 {
     const uint64_t big = 1ULL << 40;
     int kind = -1;
@@ -215,7 +215,6 @@ int read_payload(Reader &r, shtb_plan_s *p, FILE *f)
         *fp = idx ? p->allocations[idx - 1] : nullptr;
     }
     p->stats = st;
-    (void)f;
     return SHTB_OK;
 }
 
@@ -278,8 +277,8 @@ int plan_load(shtb_plan_s *p, const char *path)
     }
     Reader r{f};
     r.limit = h.payload_bytes;
-    int rc = read_payload(r, p, f);
-    if (!rc && r.ok && p->partner) rc = read_payload(r, p->partner, f);
+    int rc = read_payload(r, p);
+    if (!rc && r.ok && p->partner) rc = read_payload(r, p->partner);
     if (rc) {
         fclose(f);
         return rc;
