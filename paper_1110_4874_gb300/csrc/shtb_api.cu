@@ -311,6 +311,7 @@ void combine_polarised_stats(shtb_plan_s *p)
 
 int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts, shtb_plan *out)
 {
+    NvtxRange nvtx("shtb_plan_create");
     if (!out) return shtb_fail(SHTB_EINVAL, "out is NULL");
     *out = nullptr;
     if (nside < 1) return shtb_fail(SHTB_EINVAL, "nside must be >= 1");
@@ -363,6 +364,7 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
 
 int shtb_plan_save(shtb_plan p, const char *path)
 {
+    NvtxRange nvtx("shtb_plan_save");
     if (!p || !path) return shtb_fail(SHTB_EINVAL, "plan or path is NULL");
     int prev = -1;
     SHTB_CUDA_TRY(cudaGetDevice(&prev));
@@ -374,6 +376,7 @@ int shtb_plan_save(shtb_plan p, const char *path)
 
 int shtb_plan_load(const char *path, const shtb_plan_opts *opts, shtb_plan *out)
 {
+    NvtxRange nvtx("shtb_plan_load");
     if (!out || !path) return shtb_fail(SHTB_EINVAL, "out or path is NULL");
     *out = nullptr;
     auto t0 = std::chrono::steady_clock::now();
@@ -443,6 +446,7 @@ int shtb_plan_reserve(shtb_plan p, int nmaps)
 
 int shtb_synthesize(shtb_plan p, const double *alm_dev, double *map_dev, int nmaps, void *stream)
 {
+    NvtxRange nvtx("shtb_synthesize");
     int rc = check_call(p, alm_dev, map_dev, nmaps);
     if (rc) return rc;
     return run_synthesis(p, (const double2 *)alm_dev, map_dev, nmaps, (cudaStream_t)stream);
@@ -450,6 +454,7 @@ int shtb_synthesize(shtb_plan p, const double *alm_dev, double *map_dev, int nma
 
 int shtb_adjoint(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps, void *stream)
 {
+    NvtxRange nvtx("shtb_adjoint");
     int rc = check_call(p, map_dev, alm_dev, nmaps);
     if (rc) return rc;
     return run_adjoint(p, map_dev, (double2 *)alm_dev, nmaps, (cudaStream_t)stream);
@@ -534,6 +539,7 @@ extern "C" {
 
 int shtb_synthesize_spin(shtb_plan p, const double *alm_dev, double *map_dev, int npairs, void *stream)
 {
+    NvtxRange nvtx("shtb_synthesize_spin");
     int rc = check_spin(p, alm_dev, map_dev, npairs, "shtb_synthesize_spin");
     if (rc) return rc;
     return run_synthesis_spin(p, (const double2 *)alm_dev, map_dev, npairs, (cudaStream_t)stream);
@@ -541,6 +547,7 @@ int shtb_synthesize_spin(shtb_plan p, const double *alm_dev, double *map_dev, in
 
 int shtb_adjoint_spin(shtb_plan p, const double *map_dev, double *alm_dev, int npairs, void *stream)
 {
+    NvtxRange nvtx("shtb_adjoint_spin");
     int rc = check_spin(p, map_dev, alm_dev, npairs, "shtb_adjoint_spin");
     if (rc) return rc;
     return run_adjoint_spin(p, map_dev, (double2 *)alm_dev, npairs, (cudaStream_t)stream);
@@ -549,6 +556,7 @@ int shtb_adjoint_spin(shtb_plan p, const double *map_dev, double *alm_dev, int n
 int shtb_analyze_spin(shtb_plan p, const double *map_dev, double *alm_dev, int npairs,
                       const double *ring_weight_dev, int niter, void *stream)
 {
+    NvtxRange nvtx("shtb_analyze_spin");
     int rc = check_spin(p, map_dev, alm_dev, npairs, "shtb_analyze_spin");
     if (rc || (rc = check_analysis_args(map_dev, alm_dev, niter))) return rc;
     const int nm = 2 * npairs;
@@ -564,6 +572,7 @@ int shtb_analyze_spin(shtb_plan p, const double *map_dev, double *alm_dev, int n
 int shtb_analyze(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps,
                  const double *ring_weight_dev, int niter, void *stream)
 {
+    NvtxRange nvtx("shtb_analyze");
     int rc = check_call(p, map_dev, alm_dev, nmaps);
     if (rc || (rc = check_analysis_args(map_dev, alm_dev, niter))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -578,6 +587,7 @@ int shtb_analyze(shtb_plan p, const double *map_dev, double *alm_dev, int nmaps,
 int shtb_synthesize_host(shtb_plan p, const double *alm_host, double *map_host, int nmaps,
                          void *stream)
 {
+    NvtxRange nvtx("shtb_synthesize_host");
     int rc = check_call(p, alm_host, map_host, nmaps);
     if (rc) return rc;
     if ((rc = ensure_ws(p, nmaps))) return rc;
@@ -600,6 +610,7 @@ int shtb_synthesize_host(shtb_plan p, const double *alm_host, double *map_host, 
 
 int shtb_adjoint_host(shtb_plan p, const double *map_host, double *alm_host, int nmaps, void *stream)
 {
+    NvtxRange nvtx("shtb_adjoint_host");
     int rc = check_call(p, map_host, alm_host, nmaps);
     if (rc) return rc;
     if ((rc = ensure_ws(p, nmaps))) return rc;

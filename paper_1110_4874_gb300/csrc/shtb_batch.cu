@@ -644,6 +644,7 @@ int shtb_batch_create(const shtb_request *reqs, int nreq, const shtb_batch_opts 
 
 int shtb_batch_run(shtb_batch b, void *stream)
 {
+    NvtxRange nvtx("shtb_batch_run");
     if (!b) return shtb_fail(SHTB_EINVAL, "batch is NULL");
     int dev = -1;
     SHTB_CUDA_TRY(cudaGetDevice(&dev));

@@ -2,6 +2,7 @@
 // C-ABI layer.  Nothing here is part of the public interface (include/shtb.h).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -13,6 +14,15 @@
 // ---------------------------------------------------------------- errors
 // Record a detailed message for shtb_last_error_message() and return code.
 int shtb_fail(int code, const std::string &msg);
+
+// NVTX range over one library call (header-only NVTX 3: free unless a
+// profiler is attached), so that timelines show the calls by name
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define SHTB_CUDA_TRY(expr)                                                            \
     do {                                                                               \
