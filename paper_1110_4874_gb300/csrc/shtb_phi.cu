@@ -34,8 +34,19 @@ constexpr int phi_threads()
     return KIND == kBluestein ? 512 : 256;
 }
 
+// CTAs per SM the synthesis kernels are compiled for: the common mixed-radix
+// kind fits in 64 registers without spilling, so four share an SM wherever
+// their shared memory allows it (transforms of up to 3.5k points); the
+// radix-11/13 kind keeps two per SM (128 registers) and Bluestein one (512
+// threads).  The adjoint kernels need more registers and keep the default.
 template <int KIND>
-__global__ void __launch_bounds__(phi_threads<KIND>())
+constexpr int phi_synth_min_blocks()
+{
+    return KIND == kDirect ? 4 : KIND == kDirectBig ? 2 : 1;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(phi_threads<KIND>(), phi_synth_min_blocks<KIND>())
 phi_synth_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ q,
                  double *__restrict__ map)
 {
@@ -55,7 +66,7 @@ struct MapOut {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(phi_threads<KIND>())
+__global__ void __launch_bounds__(phi_threads<KIND>(), phi_synth_min_blocks<KIND>())
 phi_synth_qt_kernel(PlanView v, const int *__restrict__ rings, const double2 *__restrict__ qt,
                     MapOut mo, int b0)
 {
