@@ -112,6 +112,14 @@ typedef struct {
                                        element and byte counts cover both operators  */
 } shtb_plan_stats_t;
 
+/*
+ * sizeof of the public structs as this library was compiled, so that a
+ * binding can check its own layouts: opts = shtb_plan_opts, stats =
+ * shtb_plan_stats_t, request = shtb_request, batch_opts = shtb_batch_opts.
+ * Any pointer may be NULL.  Needs no GPU.  Returns SHTB_OK.
+ */
+int shtb_struct_sizes(int *opts, int *stats, int *request, int *batch_opts);
+
 /* Fill *opts with defaults.  Returns SHTB_EINVAL on NULL. */
 int shtb_plan_opts_init(shtb_plan_opts *opts);
 

@@ -125,6 +125,7 @@ SIGNATURES = {
     "shtb_test_host_butterfly": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "shtb_test_host_spin_column": (_I, [_I, _I, _I, _I, _I, _DP]),
+    "shtb_struct_sizes": (_I, [ctypes.POINTER(_I)] * 4),
 }
 
 _lib = None
@@ -428,6 +429,13 @@ def shtb_test_host_spin_column(nside: int, lmax: int, m: int, s: int, r: int):
     _check(lib().shtb_test_host_spin_column(nside, lmax, m, s, r, out.ctypes.data_as(_DP)),
            "shtb_test_host_spin_column")
     return out
+
+
+def shtb_struct_sizes() -> dict:
+    """sizeof of the public structs in the compiled library."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().shtb_struct_sizes(*[ctypes.byref(x) for x in v]), "shtb_struct_sizes")
+    return dict(zip(("opts", "stats", "request", "batch_opts"), (x.value for x in v)))
 
 
 def shtb_batch_opts_init() -> BatchOpts:

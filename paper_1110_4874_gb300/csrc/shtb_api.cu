@@ -222,6 +222,15 @@ const char *shtb_strerror(int code)
 
 const char *shtb_last_error_message(void) { return g_last_error.c_str(); }
 
+int shtb_struct_sizes(int *opts, int *stats, int *request, int *batch_opts)
+{
+    if (opts) *opts = (int)sizeof(shtb_plan_opts);
+    if (stats) *stats = (int)sizeof(shtb_plan_stats_t);
+    if (request) *request = (int)sizeof(shtb_request);
+    if (batch_opts) *batch_opts = (int)sizeof(shtb_batch_opts);
+    return SHTB_OK;
+}
+
 int shtb_plan_opts_init(shtb_plan_opts *o)
 {
     if (!o) return shtb_fail(SHTB_EINVAL, "opts is NULL");

@@ -1,12 +1,13 @@
 // Plan cache files: a built plan (host tables and every device array) written
-// to disk and read back, so that a plan whose build takes minutes on the host
-// (about 136 s at Nside = 2048, L = 4096) loads in the time it takes to read
-// it.  The paper keeps its precomputed data in files too and excludes their
-// load time from its timings; so do we.
+// to disk and read back, so that a plan whose build takes a minute or more
+// (Nside = 2048, L = 4096) loads in the time it takes to read it.  The paper
+// keeps its precomputed data in files too and excludes their load time from
+// its timings; so do we.
 //
-// Layout: a fixed header (magic, format version, the plan key, payload size,
-// FNV-1a 64 checksum of the payload), then the payload: the plan's scalars
-// and host vectors, every device array in allocation order, and the device
+// Layout: a fixed header (magic, format version, the plan key including the
+// spin, payload size, FNV-1a 64 checksum of the payload), then one payload per
+// operator (two for a polarised plan, F+ then F-): the plan's scalars and
+// host vectors, every device array in allocation order, and the device
 // pointers of the plan as indices into that array list.  A load checks the
 // magic, version, key, sizes and checksum before the plan is used; any
 // mismatch is SHTB_ECORRUPT, an unreadable file SHTB_EIO.

@@ -59,3 +59,11 @@ def test_plan_create_argument_errors_need_no_gpu():
     assert sh.lib().shtb_plan_create(8, 8, float("nan"), None, ctypes.byref(h)) == sh.SHTB_EINVAL
     assert sh.lib().shtb_plan_create(8, 8, 0.0, None, None) == sh.SHTB_EINVAL
     assert sh.lib().shtb_plan_destroy(None) == 0
+
+
+def test_binding_struct_layouts_match_the_library():
+    """The ctypes mirrors of the public structs have the library's sizes (a
+    short mirror would let the library write past it)."""
+    got = sh.shtb_struct_sizes()
+    assert got == {"opts": ctypes.sizeof(sh.PlanOpts), "stats": ctypes.sizeof(sh.PlanStats),
+                   "request": ctypes.sizeof(sh.Request), "batch_opts": ctypes.sizeof(sh.BatchOpts)}
