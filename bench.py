@@ -55,17 +55,19 @@ NCU_TRAFFIC = {
     },
     # butterfly kernels: DRAM bytes of all launches of one synthesis of 8 maps at
     # Nside=2048, L=4096 (1-pass ncu capture of the full workload), keyed on the
-    # files that define the kernels; the plan then was host-built, and a
-    # GPU-built plan differs from it by about 1e-8 in its element counts
+    # item bodies and the kernel's own definition; the plan then was host-built,
+    # and a GPU-built plan differs from it by about 1e-8 in its element counts
     "bf_level_kernel": {
-        "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu"],
-        "sha256": "d5b387ec20aacb1749fe815f3bcda7f436ca652fdc5dd4fcf15f4030c3b01217",
+        "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh",
+                    "paper_1110_4874_gb300/csrc/shtb_butterfly.cu::bf_level_kernel"],
+        "sha256": "55cd9fa108eb7ea040425787bafa55815b8a58fd294b5d2aec6422c8f52ff3c7",
         "bytes": 61_900_000_000 + 24_990_000_000,     # read + write over the 6 level launches
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
     "bf_r_kernel": {
-        "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh", "paper_1110_4874_gb300/csrc/shtb_butterfly.cu"],
-        "sha256": "d5b387ec20aacb1749fe815f3bcda7f436ca652fdc5dd4fcf15f4030c3b01217",
+        "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh",
+                    "paper_1110_4874_gb300/csrc/shtb_butterfly.cu::bf_r_kernel"],
+        "sha256": "f66591a5916bb55acbf571456d7935f46bc290398a3bd82f42c13c0c779716f1",
         "bytes": 10_720_000_000 + 3_640_000_000,
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
@@ -85,14 +87,34 @@ def file_sha256(path):
         return hashlib.sha256(fh.read()).hexdigest()
 
 
+def kernel_text(src, name):
+    """The text of the __global__ function `name` in a CUDA source: from its
+    __global__ through the brace that closes its body."""
+    i = src.find(name + "(")
+    while i >= 0:
+        g = src.rfind("__global__", 0, i)
+        if g >= 0 and ";" not in src[g:i] and "}" not in src[g:i]:
+            depth = 0
+            for k in range(src.index("{", i), len(src)):
+                depth += {"{": 1, "}": -1}.get(src[k], 0)
+                if depth == 0:
+                    return src[g:k + 1]
+        i = src.find(name + "(", i + 1)
+    raise KeyError(name)
+
+
 def sources_sha256(paths):
-    """One digest over several source files (a single file: its own sha256)."""
-    if len(paths) == 1:
+    """One digest over several sources: a path stands for the whole file,
+    "path::kernel" for that kernel's definition only (a single whole file:
+    its own sha256)."""
+    if len(paths) == 1 and "::" not in paths[0]:
         return file_sha256(paths[0])
     h = hashlib.sha256()
     for path in paths:
-        with open(os.path.join(ROOT, path), "rb") as fh:
-            h.update(fh.read())
+        fname, _, kernel = path.partition("::")
+        with open(os.path.join(ROOT, fname), "rb") as fh:
+            data = fh.read()
+        h.update(kernel_text(data.decode(), kernel).encode() if kernel else data)
     return h.hexdigest()
 
 
