@@ -356,16 +356,13 @@ def run_ours(args, rank, world, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Gaussian a_lm, C_l = 1/(l+1)^2)",
-        "config": {"workload": f"HEALPix synthesis Nside={N} L={L} batch of {B} maps",
-                   "nside": N, "lmax": L, "nmaps": B, "eps_requested": args.eps,
-                   "eps_plan": eps_plan, "compressed": bool(st["compressed"]), "leaf_cols": args.leaf_cols,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (1.07 GB a_lm, 3.2 GB maps per 8 maps)"},
+        "config": workload_config(args, world),
         "roofline": roofline, "hbm": hbm, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clocks,
         "details": {"adjoint_ms_per_map": round(ms_adj, 4), "plain_ms_per_map": round(ms_plain, 4),
                     "batched_over_plain": round(ms_plain / value, 3),
                     "stage_ms_per_step": {k: round(v / max(ncalls, 1), 3) for k, v in stages.items() if v},
+                    "eps_plan": eps_plan, "compressed": bool(st["compressed"]),
                     "plan_build_s": round(plan_s, 2), "plan_built_on": "host" if args.host_build else "gpu",
                     "plan_device_gb": round(st["plan_device_bytes"] / 1e9, 3),
                     "n_recurrence": st["n_recurrence"], "n_dense": st["n_dense"],
@@ -534,6 +531,20 @@ def plan_build_compare(sh, N=512, L=1024, eps=1e-10):
     return out
 
 
+def workload_config(args, world):
+    """The workload both arms report (the same object for ours and the
+    reference): the synthesis size, batch, requested tolerance and layout."""
+    N, L, B = args.nside, args.lmax, args.nmaps
+    gb = lambda x: round(x / 1e9, 2)  # noqa: E731
+    a_bytes, m_bytes = 16 * B * (L + 1) * (L + 2) / 2, 8 * B * 12 * N * N
+    return {"workload": f"HEALPix synthesis Nside={N} L={L} batch of {B} maps",
+            "nside": N, "lmax": L, "nmaps": B, "eps": args.eps, "leaf_cols": args.leaf_cols,
+            "parallelism": f"replicas x{world}",
+            "l2": (f"a_lm {gb(a_bytes)} GB and maps {gb(m_bytes)} GB per step, "
+                   + ("both larger than the 129 MB L2" if min(a_bytes, m_bytes) > 129e6
+                      else "not both larger than the 129 MB L2"))}
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: each step a bounded ring sample."""
     vals = []
@@ -551,9 +562,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall * 1e3 / args.steps, 1),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Gaussian a_lm, C_l = 1/(l+1)^2)", "impl": "reference",
-        "config": {"workload": f"HEALPix synthesis Nside={args.nside} L={args.lmax} batch of {args.nmaps} maps",
-                   "nside": args.nside, "lmax": args.lmax, "nmaps": args.nmaps,
-                   "eps_requested": args.eps},
+        "config": workload_config(args, args.gpus),
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
