@@ -67,3 +67,28 @@ def test_binding_struct_layouts_match_the_library():
     got = sh.shtb_struct_sizes()
     assert got == {"opts": ctypes.sizeof(sh.PlanOpts), "stats": ctypes.sizeof(sh.PlanStats),
                    "request": ctypes.sizeof(sh.Request), "batch_opts": ctypes.sizeof(sh.BatchOpts)}
+
+
+def test_host_side_rejections_need_no_gpu():
+    """Argument checks that fail before any device work: a spin other than 0
+    or 2, host tensors handed to device calls, wrong dtypes and layouts, and
+    NULL plans or files."""
+    import torch
+    opts = sh.shtb_plan_opts_init()
+    assert opts.spin == 0 and opts.gpu_build == 0
+    opts.spin = 1
+    h = ctypes.c_void_p()
+    assert sh.lib().shtb_plan_create(8, 16, 1e-10, ctypes.byref(opts), ctypes.byref(h)) == sh.SHTB_EINVAL
+    cpu = torch.zeros((1, 10), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="CUDA"):
+        sh.shtb_synthesize(None, cpu, torch.zeros((1, 12), dtype=torch.float64), 1)
+    if torch.cuda.is_available():
+        pytest.skip("the dtype and layout checks below are exercised by the GPU suite")
+    for name in ("shtb_synthesize", "shtb_adjoint", "shtb_analyze", "shtb_synthesize_spin",
+                 "shtb_adjoint_spin", "shtb_analyze_spin"):
+        fn = getattr(sh.lib(), name)
+        args = [None, None, None, 1] + ([None, 0] if "analyze" in name else []) + [None]
+        assert fn(*args) == sh.SHTB_EINVAL, name
+    assert sh.lib().shtb_plan_save(None, b"x") == sh.SHTB_EINVAL
+    assert sh.lib().shtb_plan_load(None, None, ctypes.byref(h)) == sh.SHTB_EINVAL
+    assert sh.lib().shtb_plan_load(b"/nonexistent/plan.bin", None, ctypes.byref(h)) == sh.SHTB_EIO
