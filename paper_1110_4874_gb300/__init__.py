@@ -502,7 +502,14 @@ def shtb_test_batch_stall(batch, on: bool) -> None:
 
 # ------------------------------------------------------------ convenience
 class Plan:
-    """A synthesis plan on one CUDA device (owns its device memory)."""
+    """A synthesis plan on one CUDA device (owns its device memory).
+
+    eps <= 0 gives the uncompressed transform, eps > 0 the butterfly-compressed
+    one.  Keyword options are those of shtb_plan_create: spin=2 for a
+    polarised plan (synthesize_spin / adjoint_spin / analyze_spin),
+    gpu_build=True to batch the plan's decompositions on the GPU,
+    cache_dir=... to keep plan files, and leaf_cols, max_depth, rho,
+    nthreads, device."""
 
     def __init__(self, nside: int, lmax: int, eps: float = 0.0, **opts):
         import torch
