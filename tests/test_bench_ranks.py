@@ -70,3 +70,26 @@ def test_bench_rejects_short_warmup(warmup):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", str(warmup)],
                        capture_output=True, text=True, timeout=300)
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_reference_arm_line_on_rank_zero():
+    """The reference arm (the CPU oracle on a bounded ring sample) prints one
+    JSON line with the contract's keys and the same workload config object
+    as the GPU arm would."""
+    import json
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--nside", "16", "--lmax", "32", "--steps", "1", "--warmup", "3",
+                        "--ref-rings", "8"], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is False and line["value"] > 0
+
+    class Args:
+        nside, lmax, nmaps, eps, leaf_cols = 16, 32, 8, 1e-10, 32
+    assert line["config"] == bench.workload_config(Args, 1)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
