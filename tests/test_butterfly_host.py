@@ -104,3 +104,44 @@ def test_spin_columns_match_the_oracle(nside, lmax):
                 tol = 5e-11 if r < nside // 2 else 2e-12
                 # the builder drops values below 1e-30 (Appendix crop)
                 assert np.abs(got - want).max() <= tol * np.abs(want).max() + 1e-30, (r, m, s)
+
+
+def test_id_invariants_on_legendre_blocks():
+    """The ID guarantees of Sec. 3.1 on blocks of the Legendre matrix: the
+    interpolation matrix [I | T] has every entry of modulus <= 2 (guaranteed
+    for a strong rank-revealing QR; the column-pivoted QR used here meets it
+    on these blocks with room to spare), smallest singular value >= 1, and
+    spectral norm <= sqrt(4 k (n - k) + 1)."""
+    nside, lmax = 256, 512
+    rings = oracle.healpix_rings(nside)
+    for m, (r0, r1), (c0, c1) in [(0, (100, 356), (30, 94)), (200, (0, 120), (300, 364)),
+                                  (10, (256, 503), (0, 64)), (50, (0, 230), (200, 328))]:
+        P = np.array([oracle.legendre(m, lmax, rings.z[c], rings.sinth[c]) for c in range(c0, c1)]).T
+        A = np.ascontiguousarray(P[r0:min(r1, P.shape[0])])
+        n = A.shape[1]
+        for eps in (1e-6, 1e-10, 1e-13):
+            k, skel, T = sh.shtb_test_host_id(A, eps)
+            assert np.abs(T).max() <= 2.0
+            s = np.linalg.svd(T, compute_uv=False)
+            assert s[-1] >= 1.0 - 1e-12
+            assert s[0] <= math.sqrt(4 * k * (n - k) + 1)
+
+
+@pytest.mark.parametrize("nside,lmax", [(4, 8), (8, 12), (16, 20)])
+def test_depth_zero_chains_are_the_dense_operator(nside, lmax):
+    """Where compression does not pay, the chain keeps depth 0: its stored
+    residual blocks are the dense Legendre matrix, and applying them equals
+    the dense product up to the order of the sums."""
+    seen = 0
+    for m in range(lmax + 1):
+        for t in (0, 1):
+            n = (lmax - m - t) // 2 + 1
+            if n <= 0:
+                continue
+            a = np.random.default_rng(100 * m + t).standard_normal(n)
+            q, qe, info = sh.shtb_test_host_butterfly(nside, lmax, 1e-10, m, t, a)
+            if info["depth"] == 0:
+                seen += 1
+                assert info["n_dense"] == 0 and info["n_ident"] == 0
+                np.testing.assert_allclose(q, qe, rtol=0, atol=1e-15 * max(np.abs(qe).max(), 1e-300))
+    assert seen > 0
