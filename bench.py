@@ -234,7 +234,8 @@ def run_ours(args, rank, world, dist):
     t0 = time.perf_counter()
     eps_plan = args.eps
     try:
-        plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols, gpu_build=not args.host_build)
+        plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols, gpu_build=not args.host_build,
+                       nthreads=build_threads(world, not args.host_build))
     except sh.ShtbError as e:
         if e.code != sh.SHTB_ENOTSUP or eps_plan <= 0:
             raise
@@ -529,6 +530,17 @@ def plan_build_compare(sh, N=512, L=1024, eps=1e-10):
         out["n_dense_" + name[:-2]] = p.stats()["n_dense"]
         p.close()
     return out
+
+
+def build_threads(world, gpu_build):
+    """Host threads for one rank's plan build: the library's default (all
+    cores, twice that for the GPU builder, whose workers also wait on their
+    GPU batches) on one rank; the node's cores shared out when several ranks
+    build at once."""
+    if world <= 1:
+        return 0
+    cores = max(1, (os.cpu_count() or 1) // world)
+    return 2 * cores if gpu_build else cores
 
 
 def workload_config(args, world):

@@ -93,3 +93,10 @@ def test_reference_arm_line_on_rank_zero():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_plan_build_threads_are_shared_between_ranks():
+    assert bench.build_threads(1, True) == 0 and bench.build_threads(1, False) == 0
+    cores = os.cpu_count() or 1
+    assert bench.build_threads(2, False) == max(1, cores // 2)
+    assert bench.build_threads(8, True) == 2 * max(1, cores // 8)
