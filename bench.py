@@ -233,9 +233,19 @@ def run_ours(args, rank, world, dist):
 
     t0 = time.perf_counter()
     eps_plan = args.eps
+    built_on = "host" if args.host_build else "gpu"
     try:
-        plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols, gpu_build=not args.host_build,
-                       nthreads=build_threads(world, not args.host_build))
+        try:
+            plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols, gpu_build=not args.host_build,
+                           nthreads=build_threads(world, not args.host_build))
+        except sh.ShtbError as e:
+            # the GPU builder needs pinned staging per host worker; where the
+            # host cannot give it, the same plan is built with host IDs
+            if args.host_build or e.code not in (sh.SHTB_ENOMEM, sh.SHTB_ECUDA):
+                raise
+            built_on = f"host (GPU builder: {e})"
+            plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols,
+                           nthreads=build_threads(world, False))
     except sh.ShtbError as e:
         if e.code != sh.SHTB_ENOTSUP or eps_plan <= 0:
             raise
@@ -364,7 +374,7 @@ def run_ours(args, rank, world, dist):
                     "batched_over_plain": round(ms_plain / value, 3),
                     "stage_ms_per_step": {k: round(v / max(ncalls, 1), 3) for k, v in stages.items() if v},
                     "eps_plan": eps_plan, "compressed": bool(st["compressed"]),
-                    "plan_build_s": round(plan_s, 2), "plan_built_on": "host" if args.host_build else "gpu",
+                    "plan_build_s": round(plan_s, 2), "plan_built_on": built_on,
                     "plan_device_gb": round(st["plan_device_bytes"] / 1e9, 3),
                     "n_recurrence": st["n_recurrence"], "n_dense": st["n_dense"],
                     "n_rstored": st["n_rstored"], "n_ident": st["n_ident"],
