@@ -240,8 +240,9 @@ def run_ours(args, rank, world, dist):
                            nthreads=build_threads(world, not args.host_build))
         except sh.ShtbError as e:
             # the GPU builder needs pinned staging per host worker; where the
-            # host cannot give it, the same plan is built with host IDs
-            if args.host_build or e.code not in (sh.SHTB_ENOMEM, sh.SHTB_ECUDA):
+            # host cannot give it (SHTB_ENOMEM), the same plan is built with
+            # host IDs.  Any other error, a CUDA fault above all, propagates.
+            if args.host_build or e.code != sh.SHTB_ENOMEM:
                 raise
             built_on = f"host (GPU builder: {e})"
             plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols,
@@ -327,17 +328,20 @@ def run_ours(args, rank, world, dist):
            "h2d_bytes_per_step": int(alm_h.numel() * alm_h.element_size()),
            "d2h_bytes_per_step": int(maps_h.numel() * maps_h.element_size())}
 
-    # ---- roofline of the dominant kernel (FP64-bound on GB300)
+    # ---- roofline of the dominant kernel (FP64-bound on GB300), on the
+    # algorithmic count of the butterfly: 4 flop per map per stored dense
+    # element (two FMAs on the real and imaginary parts); identity entries
+    # are a copy and count no flop
     groups = [8] * (B // 8) + ([B % 8] if B % 8 else [])
+    ncall = max(ncalls, 1)
     if st["compressed"]:
         per_step = {   # kernel -> (algorithmic flops per step, ms per step)
-            "bf_level_kernel": (B * (4.0 * st["n_dense"] + 2.0 * st["n_ident"]),
-                                stages["bf_levels"] / max(ncalls, 1)),
-            "bf_r_kernel": (B * 4.0 * st["n_rstored"], stages["bf_residual"] / max(ncalls, 1)),
+            "bf_level_kernel": (B * 4.0 * st["n_dense"], stages["bf_levels"] / ncall),
+            "bf_r_kernel": (B * 4.0 * st["n_rstored"], stages["bf_residual"] / ncall),
         }
     else:
         per_step = {"legendre_synth_kernel": (sum(4.0 * st["n_recurrence"] * (1 + g) for g in groups),
-                                              stages["legendre_synth"] / max(ncalls, 1))}
+                                              stages["legendre_synth"] / ncall)}
     kname = max(per_step, key=lambda k: per_step[k][1])
     flops, kms = per_step[kname]
     achieved = flops / (kms * 1e-3) / 1e12
@@ -345,13 +349,30 @@ def run_ours(args, rank, world, dist):
     rec = NCU_TRAFFIC.get(kname)
     if rec and rec["bytes"] and rec["sha256"] == sources_sha256(rec["sources"]):
         traffic = rec["bytes"]
+    dfma_gflops, _ = sh.shtb_measure_fp64_peak(local)
+    peak_meas = dfma_gflops / 1e3
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "kernel": f"{kname} (FP64 pipe)",
                 "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "peak_measured_dfma": round(peak_meas, 4),
+                "frac_of_measured_dfma": round(achieved / peak_meas, 4),
+                "count": "4 flop per map per stored dense element; identity entries are copies",
                 "per_kernel_tflops": {k: round(f / (t * 1e-3) / 1e12, 4) if t else None
                                       for k, (f, t) in per_step.items()}}
+    if st["compressed"]:
+        with_ident = B * (4.0 * st["n_dense"] + 2.0 * st["n_ident"])
+        roofline["frac_counting_identity_adds"] = round(
+            with_ident / (per_step["bf_level_kernel"][1] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4)
     flops_leg = sum(f for f, _ in per_step.values())
+    # ring stage: a real FFT of each ring's length plus the fold of the L+1
+    # orders (2.5 J log2 J + 4 (L + 1) flop per ring and map)
+    flops_phi = B * (st["phi_flops_per_map"] + 4.0 * (L + 1) * plan.nrings)
+    phi_ms = stages["phi_synth"] / ncall
+    roofline["ring_stage"] = {"flops_per_step": flops_phi, "ms_per_step": round(phi_ms, 3),
+                              "achieved": round(flops_phi / (phi_ms * 1e-3) / 1e12, 4) if phi_ms else None,
+                              "frac": round(flops_phi / (phi_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4)
+                              if phi_ms else None}
     # whole-step HBM view (algorithmic bytes of the batch over the step time)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
@@ -361,6 +382,12 @@ def run_ours(args, rank, world, dist):
     hbm = {"bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (step_ms * 1e-3) / 1e9, 1),
            "peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json)" if hbm_peak else None,
            "frac": round(step_bytes / (step_ms * 1e-3) / 1e9 / hbm_peak, 4) if hbm_peak else None}
+    # whole step against its roofline time T* = max(bytes / BW, flops / F64)
+    t_star = max(step_bytes / (hbm_peak * 1e9) if hbm_peak else 0.0,
+                 (flops_leg + flops_phi) / (FP64_PEAK_TFLOPS * 1e12)) * 1e3
+    roofline["whole_step"] = {"flops": flops_leg + flops_phi, "bytes": step_bytes,
+                              "t_star_ms": round(t_star, 3), "t_ms": round(step_ms, 3),
+                              "t_star_over_t": round(t_star / step_ms, 4)}
 
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,

@@ -433,7 +433,10 @@ int shtb_test_legendre_adjoint(shtb_plan plan, const double *q_dev, double *alm_
  *  - The first call on a device looks up the array's device address with
  *    cudaGetSymbolAddress (that device current) and caches it; make that
  *    first call before any stream capture.  Every GPU that loads the library
- *    holds the array until the process exits.
+ *    holds the array until the process exits.  The cached address belongs
+ *    to the device's primary context: after cudaDeviceReset (or anything
+ *    else that destroys and recreates that context) this call is not
+ *    supported in the same process.
  *  - All calls share the one array, which keeps the last call's contents:
  *    calls whose work overlaps on the GPU (other streams, other threads)
  *    race on it and must be ordered by the caller.  No state is carried from

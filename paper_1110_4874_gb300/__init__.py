@@ -238,11 +238,50 @@ def shtb_plan_reserve(plan, nmaps: int) -> None:
     _check(lib().shtb_plan_reserve(plan, nmaps), "shtb_plan_reserve")
 
 
+# Per call: the layouts of its input and output (see include/shtb.h) and the
+# fields per transform unit (a polarised pair carries two of each).
+_LAYOUTS = {
+    "shtb_synthesize": ("alm", "map", 1),
+    "shtb_synthesize_noalloc": ("alm", "map", 1),
+    "shtb_adjoint": ("map", "alm", 1),
+    "shtb_synthesize_spin": ("alm", "map", 2),
+    "shtb_adjoint_spin": ("map", "alm", 2),
+    "shtb_test_legendre": ("alm", "q", 1),
+    "shtb_test_butterfly": ("alm", "qt", 1),
+    "shtb_test_phi": ("q", "map", 1),
+    "shtb_test_phi_adjoint": ("map", "q", 1),
+    "shtb_test_legendre_adjoint": ("q", "alm", 1),
+}
+
+
+def _layout_elems(st, layout):
+    """Elements (complex or real, as the layout's dtype) of one field."""
+    L = st["lmax"]
+    return {"alm": st["nalm"], "map": st["npix"], "q": st["nrings"] * (L + 1),
+            "qt": 2 * 2 * st["nside"] * (L + 1)}[layout]
+
+
+def _check_sizes(name, plan, tensors, nmaps):
+    """Refuse tensors smaller than the call reads or writes: the kernels
+    trust the sizes, so a short buffer would mean out-of-bounds device
+    accesses.  tensors: (input, output) in the order of _LAYOUTS[name]."""
+    if int(nmaps) < 1:
+        return          # the library rejects it with SHTB_EINVAL
+    st = shtb_plan_stats(plan)
+    src_l, dst_l, fields = _LAYOUTS[name]
+    for t, layout, what in zip(tensors, (src_l, dst_l), ("input", "output")):
+        need = int(nmaps) * fields * _layout_elems(st, layout)
+        if t.numel() < need:
+            raise ValueError(f"{name}: {what} holds {t.numel()} elements, the call needs "
+                             f"{need} ({nmaps} x {fields} x {layout} of nside={st['nside']}, "
+                             f"lmax={st['lmax']})")
+
+
 def _call_dev(name, plan, src, src_dtype, dst, dst_dtype, nmaps, stream):
-    import torch
     fn = getattr(lib(), name)
-    _check(fn(plan, _dptr(src, src_dtype, "input"), _dptr(dst, dst_dtype, "output"), int(nmaps),
-              _stream_handle(stream)), name)
+    ps, pd = _dptr(src, src_dtype, "input"), _dptr(dst, dst_dtype, "output")
+    _check_sizes(name, plan, (src, dst), nmaps)
+    _check(fn(plan, ps, pd, int(nmaps), _stream_handle(stream)), name)
 
 
 def shtb_synthesize(plan, alm, maps, nmaps: int, stream=None) -> None:
@@ -283,8 +322,9 @@ def shtb_analyze_spin(plan, maps, alm, npairs: int, ring_weight=None, niter: int
     (Q, U) -> alm [npairs][2][nalm] (E, B); ring_weight as for shtb_analyze."""
     import torch
     w = None if ring_weight is None else _dptr(ring_weight, torch.float64, "ring_weight")
-    _check(lib().shtb_analyze_spin(plan, _dptr(maps, torch.float64, "maps"),
-                                   _dptr(alm, torch.complex128, "alm"), int(npairs), w, int(niter),
+    pm, pa = _dptr(maps, torch.float64, "maps"), _dptr(alm, torch.complex128, "alm")
+    _check_analysis_sizes("shtb_analyze_spin", plan, maps, alm, ring_weight, npairs, 2)
+    _check(lib().shtb_analyze_spin(plan, pm, pa, int(npairs), w, int(niter),
                                    _stream_handle(stream)), "shtb_analyze_spin")
 
 
@@ -294,9 +334,23 @@ def shtb_analyze(plan, maps, alm, nmaps: int, ring_weight=None, niter: int = 0,
     area 4 pi / npix) or a contiguous float64 device tensor, one per ring."""
     import torch
     w = None if ring_weight is None else _dptr(ring_weight, torch.float64, "ring_weight")
-    _check(lib().shtb_analyze(plan, _dptr(maps, torch.float64, "maps"),
-                              _dptr(alm, torch.complex128, "alm"), int(nmaps), w, int(niter),
+    pm, pa = _dptr(maps, torch.float64, "maps"), _dptr(alm, torch.complex128, "alm")
+    _check_analysis_sizes("shtb_analyze", plan, maps, alm, ring_weight, nmaps, 1)
+    _check(lib().shtb_analyze(plan, pm, pa, int(nmaps), w, int(niter),
                               _stream_handle(stream)), "shtb_analyze")
+
+
+def _check_analysis_sizes(name, plan, maps, alm, ring_weight, nmaps, fields):
+    if int(nmaps) < 1:
+        return
+    st = shtb_plan_stats(plan)
+    checks = [(maps, int(nmaps) * fields * st["npix"], "maps"),
+              (alm, int(nmaps) * fields * st["nalm"], "alm")]
+    if ring_weight is not None:
+        checks.append((ring_weight, st["nrings"], "ring_weight"))
+    for t, need, what in checks:
+        if t.numel() < need:
+            raise ValueError(f"{name}: {what} holds {t.numel()} elements, the call needs {need}")
 
 
 def _hptr(t, dtype, name):
@@ -307,6 +361,7 @@ def _hptr(t, dtype, name):
 
 def shtb_synthesize_host(plan, alm_host, maps_host, nmaps: int, stream=None) -> None:
     import torch
+    _check_sizes("shtb_synthesize", plan, (alm_host, maps_host), nmaps)
     _check(lib().shtb_synthesize_host(plan, _hptr(alm_host, torch.complex128, "alm"),
                                       _hptr(maps_host, torch.float64, "maps"), int(nmaps),
                                       _stream_handle(stream)), "shtb_synthesize_host")
@@ -314,6 +369,7 @@ def shtb_synthesize_host(plan, alm_host, maps_host, nmaps: int, stream=None) -> 
 
 def shtb_adjoint_host(plan, maps_host, alm_host, nmaps: int, stream=None) -> None:
     import torch
+    _check_sizes("shtb_adjoint", plan, (maps_host, alm_host), nmaps)
     _check(lib().shtb_adjoint_host(plan, _hptr(maps_host, torch.float64, "maps"),
                                    _hptr(alm_host, torch.complex128, "alm"), int(nmaps),
                                    _stream_handle(stream)), "shtb_adjoint_host")
@@ -458,6 +514,7 @@ def shtb_batch_create(requests, autotune: bool = True, warps_per_block: int = 0,
         arr[i].alm_dev = _dptr(alm, torch.complex128, "alm").value
         arr[i].map_dev = _dptr(maps, torch.float64, "maps").value
         arr[i].nmaps = int(alm.shape[0])
+        _check_sizes("shtb_synthesize", arr[i].plan, (alm, maps), arr[i].nmaps)
         arr[i].dir = 0
     o = shtb_batch_opts_init()
     o.autotune, o.warps_per_block, o.group_width = int(autotune), warps_per_block, group_width

@@ -55,6 +55,7 @@ int scratch_address(int dev, void **out)
 extern "C" int shtb_synthesize_noalloc(shtb_plan p, const double *alm_dev, double *map_dev,
                                        int nmaps, void *stream)
 {
+    NvtxRange range("shtb_synthesize_noalloc");
     if (!p) return shtb_fail(SHTB_EINVAL, "plan is NULL");
     if (p->kind != 0) return shtb_fail(SHTB_ENOTSUP, "a polarised plan serves shtb_synthesize_spin only");
     if (!alm_dev || !map_dev) return shtb_fail(SHTB_EINVAL, "NULL buffer");

@@ -1,10 +1,22 @@
 """Parity at the configured full sizes, in the launch configuration bench.py
-times (one synthesize call over all maps of a plan), on outputs the oracle can
-compute one by one: whole rings sampled at both poles, the equator, the
-polar-cap / belt boundaries and at random in between.  Rule of the other
-parity tests (Eq. relative-error over the sampled pixels): <= 1e-10 at
-eps = 1e-12, <= 100 eps otherwise.  The adjoint is checked at full size by the
-dot-product identity <Y a, f> = <a, Y^T f>, which holds at any size."""
+times (one call over all maps of a plan), on outputs the oracle can compute
+one by one.
+
+* Synthesis: whole rings sampled at both poles, the equator, the polar-cap /
+  belt boundaries and at random in between, against ``oracle.synthesize`` on
+  those rings.
+* Adjoint: a map that is zero outside such a ring sample; its transpose
+  Y^T f then only sums over the sampled rings, so ``oracle.adjoint`` on the
+  sample gives every a_lm exactly.
+
+Rules (relative RMS, Eq. relative-error): <= 1e-12 for the uncompressed
+operator, <= 1e-10 at eps = 1e-12, <= 100 eps otherwise (the tolerance is not
+the error: Table accuracy reports errors of 0.4 to 3 times the requested
+tolerance).  The compressed operator is also held to <= 5 eps, just above the
+top of that range, so that a tenfold loss of accuracy fails even where the
+100 eps rule would still pass.  Plans are built once per class and freed
+before the next class builds its own (the plans at L = 4096 take tens of GB).
+"""
 import numpy as np
 import pytest
 
@@ -18,27 +30,53 @@ import paper_1110_4874_gb300 as sh  # noqa: E402
 
 
 def rel_rms(x, y):
-    return float(np.sqrt(np.sum((x - y) ** 2) / np.sum(x ** 2)))
+    x = np.asarray(x)
+    y = np.asarray(y)
+    return float(np.sqrt(np.sum(np.abs(x - y) ** 2) / np.sum(np.abs(x) ** 2)))
 
 
-def ring_sample(nside, n):
+def ring_sample(nside, n, extra_fixed=()):
+    """Ring indices (0-based, north to south): the first and last three rings,
+    the cap/belt boundaries, the equator and its neighbours, and random rings
+    up to n in all."""
     nr = 4 * nside - 1
-    fixed = [0, 1, 2, nside - 2, nside - 1, nside, 2 * nside - 2, 2 * nside - 1, 2 * nside,
-             3 * nside - 1, 3 * nside, nr - 3, nr - 2, nr - 1]
+    fixed = {0, 1, 2, nside - 2, nside - 1, nside, 2 * nside - 2, 2 * nside - 1, 2 * nside,
+             3 * nside - 1, 3 * nside, nr - 3, nr - 2, nr - 1}
+    fixed |= {int(k) for k in extra_fixed if 0 <= k < nr}
+    fixed = sorted(fixed)
     rest = np.setdiff1d(np.arange(nr), fixed)
-    extra = np.random.default_rng(nside).choice(rest, n - len(fixed), replace=False)
+    extra = np.random.default_rng(nside).choice(rest, max(n - len(fixed), 0), replace=False)
     return np.unique(np.concatenate([fixed, extra]))
 
 
-def check_rings(nside, lmax, eps, a, maps, which, nrings):
+def sampled_synthesis(nside, lmax, a, maps, which, idx):
+    """(oracle, ours) pixel arrays of maps `which` on the rings `idx`."""
     rings = oracle.healpix_rings(nside)
-    idx = ring_sample(nside, nrings)
     want = oracle.synthesize(rings.subset(idx), lmax, a[which])
     maps = maps.cpu().numpy()
     got = np.concatenate([maps[:, rings.start[k]:rings.start[k] + rings.J[k]] for k in idx], axis=1)
+    return want, got[which], rings
+
+
+def per_ring_errors(rings, idx, want, got):
+    """Relative RMS of each sampled ring (error RMS over the ring's own RMS)."""
+    out, o = [], 0
+    for k in idx:
+        J = int(rings.J[k])
+        out.append((int(k), rel_rms(want[:, o:o + J], got[:, o:o + J])))
+        o += J
+    return out
+
+
+def check_rings(nside, lmax, eps, a, maps, which, nrings):
+    idx = ring_sample(nside, nrings)
+    want, got, _ = sampled_synthesis(nside, lmax, a, maps, which, idx)
     tol = 1e-10 if eps <= 1e-12 else 100 * eps
-    for i, b in enumerate(which):
-        assert rel_rms(want[i], got[b]) <= tol, (b, rel_rms(want[i], got[b]))
+    errs = [rel_rms(want[i], got[i]) for i in range(len(which))]
+    print(f"nside={nside} lmax={lmax} eps={eps:g}: rel RMS per sampled map {errs}")
+    for b, e in zip(which, errs):
+        assert e <= tol, (b, e)
+        assert e <= 5 * eps, (b, e)
 
 
 @pytest.mark.parametrize("eps", [1e-10, 1e-12])
@@ -53,27 +91,136 @@ def test_nside512_one_and_sixteen_maps(eps):
     plan.close()
 
 
-@pytest.fixture(scope="module")
-def planck_plan():
-    # built by the GPU plan builder, as bench.py builds it
-    plan = sh.Plan(2048, 4096, 1e-10, gpu_build=True)
-    yield plan
-    plan.close()
+def adjoint_on_ring_sample(plan, nside, lmax, idx, nmaps, seed):
+    """(oracle, ours) Y^T f for maps that are white noise on the rings idx
+    and zero elsewhere."""
+    rings = oracle.healpix_rings(nside)
+    sub = rings.subset(idx)
+    fs = synthetic.gaussian_map(sub.npix, nmaps, seed=seed)
+    f = np.zeros((nmaps, rings.npix))
+    o = 0
+    for k in idx:
+        J = int(rings.J[k])
+        f[:, rings.start[k]:rings.start[k] + J] = fs[:, o:o + J]
+        o += J
+    got = plan.adjoint(torch.from_numpy(f).cuda()).cpu().numpy()
+    want = oracle.adjoint(sub, lmax, fs)
+    return want, got
 
 
-def test_nside2048_batch_of_eight(planck_plan):
-    """Nside=2048, L=4096, eps=1e-10, 8 maps in one call (the benchmark's
-    workload), maps 0 and 7 on a 24-ring sample."""
-    a = synthetic.gaussian_alm(4096, 8, seed=2048)
-    maps = planck_plan.synthesize(torch.from_numpy(a).cuda())
-    check_rings(2048, 4096, 1e-10, a, maps, [0, 7], 24)
+def class_plan(*args, **kw):
+    """A plan that lives for the tests of one class and is freed after them."""
+    p = sh.Plan(*args, **kw)
+    yield p
+    p.close()
+    torch.cuda.empty_cache()
 
 
-def test_nside2048_dot_product_identity(planck_plan):
-    a = torch.from_numpy(synthetic.gaussian_alm(4096, 2, seed=2049)).cuda()
-    f = torch.from_numpy(synthetic.gaussian_map(planck_plan.npix, 2, seed=2050)).cuda()
-    ya = planck_plan.synthesize(a)
-    ytf = planck_plan.adjoint(f)
-    lhs = float((ya * f).sum())
-    rhs = float((a.conj() * ytf).real.sum())
-    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+@pytest.fixture(scope="class")
+def planck_1e10():
+    # the benchmark's plan, built by the GPU plan builder as bench.py builds it
+    yield from class_plan(2048, 4096, 1e-10, gpu_build=True)
+
+
+@pytest.fixture(scope="class")
+def planck_1e12():
+    yield from class_plan(2048, 4096, 1e-12, gpu_build=True)
+
+
+@pytest.fixture(scope="class")
+def planck_exact():
+    yield from class_plan(2048, 4096, 0.0)
+
+
+class TestPlanck1e10:
+    """Nside=2048, L=4096, eps=1e-10 (the benchmark's plan)."""
+
+    def test_synthesis_batch_of_eight(self, planck_1e10):
+        """8 maps in one call (the benchmark's workload), maps 0 and 7 on a
+        24-ring sample."""
+        a = synthetic.gaussian_alm(4096, 8, seed=2048)
+        maps = planck_1e10.synthesize(torch.from_numpy(a).cuda())
+        check_rings(2048, 4096, 1e-10, a, maps, [0, 7], 24)
+
+    def test_adjoint_against_the_oracle(self, planck_1e10):
+        """Y^T f of two maps supported on 34 whole rings, every a_lm against
+        the oracle's transpose (Eq. wiener, real-inner-product convention)."""
+        idx = ring_sample(2048, 34)
+        want, got = adjoint_on_ring_sample(planck_1e10, 2048, 4096, idx, 2, seed=2051)
+        errs = [rel_rms(want[b], got[b]) for b in range(2)]
+        print(f"adjoint Nside=2048 L=4096 eps=1e-10 on {idx.size} rings: rel RMS {errs}")
+        for e in errs:
+            assert e <= 100 * 1e-10
+            assert e <= 5 * 1e-10
+
+    def test_dot_product_identity(self, planck_1e10):
+        a = torch.from_numpy(synthetic.gaussian_alm(4096, 2, seed=2049)).cuda()
+        f = torch.from_numpy(synthetic.gaussian_map(planck_1e10.npix, 2, seed=2050)).cuda()
+        ya = planck_1e10.synthesize(a)
+        ytf = planck_1e10.adjoint(f)
+        lhs = float((ya * f).sum())
+        rhs = float((a.conj() * ytf).real.sum())
+        assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+class TestPlanck1e12:
+    """Nside=2048, L=4096 with the tighter tolerance eps=1e-12: the maps
+    within 1e-10 of the oracle (the accuracy gate of the compressed path)."""
+
+    def test_synthesis(self, planck_1e12):
+        a = synthetic.gaussian_alm(4096, 2, seed=2052)
+        maps = planck_1e12.synthesize(torch.from_numpy(a).cuda())
+        check_rings(2048, 4096, 1e-12, a, maps, [0, 1], 28)
+
+
+class TestPlanckUncompressed:
+    """Nside=2048, L=4096 without compression (eps = 0): the jump-two
+    recurrence kernel against the oracle's one-step recurrence."""
+
+    def test_synthesis(self, planck_exact):
+        nside = 2048
+        eq = 2 * nside - 1
+        idx = ring_sample(nside, 36, extra_fixed=range(eq - 3, eq + 4))
+        a = synthetic.gaussian_alm(4096, 1, seed=2053)
+        maps = planck_exact.synthesize(torch.from_numpy(a).cuda())
+        want, got, rings = sampled_synthesis(nside, 4096, a, maps, [0], idx)
+        per_ring = per_ring_errors(rings, idx, want, got)
+        print("uncompressed Nside=2048 L=4096, rel RMS per ring (ring index, error):")
+        print(", ".join(f"{k}: {e:.2e}" for k, e in per_ring))
+        total = rel_rms(want, got)
+        print(f"over the sample: {total:.3e}")
+        assert total <= 1e-12
+        for k, e in per_ring:
+            assert e <= 1e-12, (k, e)
+
+
+class TestDifferentiationSize:
+    """The differentiation workload: Nside=1024, L=2048, 4 maps, eps=1e-10,
+    loss 0.5 ||Y a - d||^2 with d = Y a_true + 0.1 N(0, 1) per pixel.  The
+    autograd gradient (the adjoint kernels) against a central difference of
+    the loss along a random direction, exact for a quadratic loss up to
+    rounding, at 1e-9 relative."""
+
+    def test_directional_derivative(self):
+        plan = sh.Plan(1024, 2048, 1e-10, gpu_build=True)
+        B, L = 4, 2048
+        a_true = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=4100)).cuda()
+        a0 = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=4000)).cuda()
+        noise = torch.from_numpy(np.random.default_rng(4200).normal(0.0, 0.1, (B, plan.npix))).cuda()
+        with torch.no_grad():
+            d = plan.synthesize(a_true) + noise
+
+        def loss_of(a):
+            r = sh.synthesize(a, plan) - d
+            return 0.5 * (r * r).sum()
+
+        a = a0.clone().requires_grad_(True)
+        loss_of(a).backward()
+        g = a.grad.detach()
+        v = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=4300)).cuda()
+        with torch.no_grad():
+            fd = float((loss_of(a0 + 1e-3 * v) - loss_of(a0 - 1e-3 * v)) / 2e-3)
+        dd = float((g.conj() * v).real.sum())
+        print(f"directional derivative: autograd {dd:.15e}, central difference {fd:.15e}")
+        assert abs(fd - dd) <= 1e-9 * abs(dd)
+        plan.close()

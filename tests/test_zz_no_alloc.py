@@ -50,3 +50,22 @@ def test_noalloc_rejects_requests_beyond_the_static_scratch():
     torch.cuda.synchronize()
     assert torch.equal(want, got)
     plan.close()
+
+
+def test_noalloc_on_a_compressed_plan_applies_the_exact_operator():
+    """On a compressed plan (eps > 0) the call evaluates the uncompressed
+    operator from the plan's recurrence tables: bit for bit the maps of an
+    eps = 0 plan of the same size, and within the compressed plan's
+    tolerance rule (1e-10 at eps = 1e-12) of that plan's shtb_synthesize."""
+    nside, lmax, nmaps = 32, 64, 2
+    exact = sh.Plan(nside, lmax, 0.0)
+    comp = sh.Plan(nside, lmax, 1e-12)
+    for call in range(2):
+        a = torch.from_numpy(synthetic.gaussian_alm(lmax, nmaps, seed=70 + call)).cuda()
+        got = torch.full((nmaps, comp.npix), float("nan"), dtype=torch.float64, device="cuda")
+        sh.shtb_synthesize_noalloc(comp.handle, a, got, nmaps)
+        torch.cuda.synchronize()
+        assert torch.equal(got, exact.synthesize(a))
+        assert rel_rms(comp.synthesize(a), got) <= 1e-10
+    comp.close()
+    exact.close()
