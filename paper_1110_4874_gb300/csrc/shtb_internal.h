@@ -56,6 +56,17 @@ struct alignas(32) RecState {
     double cur0, prev0, cur1, prev1;
 };
 
+// Rader's algorithm for a ring transform with one prime factor p > 13
+// (its own exponent 1) whose p - 1 factors over 2, 3, 5, 7, 11, 13: the
+// p-point DFTs become cyclic convolutions of length n = p - 1.  Offsets are
+// into the plan's rad (radix list of n), rdr_int (g^v and g^{-v} mod p,
+// v < n, g a primitive root) and rdr_dbl (the position-order DFT of
+// beta_t = e^{2 pi i g^t / p} scaled by 1/n, and e^{2 pi i t / n}).
+struct RaderInfo {
+    int p, n, rl, ga, gi, pad;
+    long long G, tw;
+};
+
 // Everything a kernel needs to know about a plan, by value.
 struct PlanView {
     int nside, lmax, nrings, nhalf;   // nhalf = 2 nside rings with z >= 0 (incl. equator)
@@ -100,6 +111,17 @@ struct PlanView {
     const double2 *fb;
     const double2 *W;
     int Wlen;
+    // fold weights of the synthesis ring kernels: ab + ring_ab[ring] holds,
+    // for k < K = J/2, {A_k, B_k} with Z_k = G_k A_k + G_{k+K} B_k (G the
+    // ring's folded spectrum without its phi_0 phase); the half-pixel phase,
+    // the half-length packing and, on Bluestein rings, the chirp are in them
+    const long long *ring_ab;
+    const double2 *ab;
+    // Rader rings: ring_rdr[ring] indexes rdr (-1 for other rings)
+    const int *ring_rdr;
+    const RaderInfo *rdr;
+    const int *rdr_int;
+    const double2 *rdr_dbl;
 };
 
 struct BfPlanDev;
@@ -123,7 +145,9 @@ struct shtb_plan_s {
 
     // ring lists of the three ring-kernel variants (mixed radix: direct
     // transform of length K over radices 2..7, Bluestein, direct with a
-    // radix 11 or 13), heaviest rings first
+    // radix 11 or 13 or a Rader pass), heaviest rings first; the max_ values
+    // are the shared-memory entries (complex) of the longest ring of each
+    // (a Rader ring also holds its convolution scratch)
     std::vector<int> direct_rings, blue_rings, big_rings;
     int max_K_direct = 0, max_M_mx = 0, max_K_big = 0;
     // Bluestein rings blue_rings[blue_split..] have transforms of at most

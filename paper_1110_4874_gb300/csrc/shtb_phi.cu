@@ -99,11 +99,15 @@ phi_adjoint_kernel(PlanView v, const int *__restrict__ rings, const double *__re
     }
     if (BLUE) {
         __syncthreads();
-        bluestein_mx(sm, K, v.ring_mx[ring], T, v.mfb + v.ring_mfb[ring], rl, TwTable{v.mtw + v.ring_mtw[ring]});
+        bluestein_mx<true>(sm, K, v.ring_mx[ring], T, v.mfb + v.ring_mfb[ring], rl,
+                           TwTable{v.mtw + v.ring_mtw[ring]});
         for (int n = threadIdx.x; n < K; n += blockDim.x) sm[n] = cconj(sm[n]);
         __syncthreads();
     } else {
-        fft_mx_dif<KIND == kDirectBig>(sm, K, rl, TwRing{T, J});   // position order
+        constexpr bool BIG = KIND == kDirectBig;
+        RaderCtx rc;
+        const RaderCtx *rcp = BIG ? rader_ctx(v, ring, K, sm, rc) : nullptr;
+        fft_mx_dif<BIG, BIG>(sm, K, K, rl, TwRing{T, J}, rcp);   // position order
     }
 
     // F_r = E'_r + e^{-2 pi i r/J} O'_r with E' = (Zf_r + conj Zf_{K-r})/2,

@@ -23,6 +23,17 @@ __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b)   // a * conj
 }
 __device__ __forceinline__ double2 times_i(double2 a) { return make_double2(-a.y, a.x); }
 
+// sign flips as integer operations on the sign bit (no FP64 instruction)
+__device__ __forceinline__ double dneg_if(double x, int neg)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(neg & 1) << 63));
+}
+__device__ __forceinline__ double2 cneg_if(double2 a, int neg)
+{
+    return make_double2(dneg_if(a.x, neg), dneg_if(a.y, neg));
+}
+__device__ __forceinline__ double2 cconj_i(double2 a) { return make_double2(a.x, dneg_if(a.y, 1)); }
+
 // e^{i pi n / J} for any integer n >= 0 from the half-circle table T (n < J)
 __device__ __forceinline__ double2 ring_root(const double2 *__restrict__ T, int J, long long n)
 {
@@ -32,30 +43,43 @@ __device__ __forceinline__ double2 ring_root(const double2 *__restrict__ T, int 
     return make_double2(-t.x, -t.y);
 }
 
-// G_r = sum over m = r (mod J), |m| <= L, of (-1)^{s t} q_m  (m = r + tJ)
+// ... for 0 <= n < 2^31, in 32-bit integer arithmetic
+__device__ __forceinline__ double2 ring_root32(const double2 *__restrict__ T, int J, int n)
+{
+    const int k = n % (2 * J);
+    if (k < J) return __ldg(T + k);
+    return cneg_if(__ldg(T + (k - J)), 1);
+}
+
 template <bool CG>
 __device__ __forceinline__ double2 ldq(const double2 *p)
 {
     return CG ? __ldcg(p) : __ldg(p);
 }
 
+// G_r = sum over m = r (mod J), |m| <= L, of (-1)^{s t} q_m (m = r + tJ),
+// with q_m = conj(q_{-m}) for m < 0.  The first term starts the sum (no add
+// to zero) and the signs are flipped bitwise, so every FP64 instruction here
+// is one of the sum's additions.
 template <class QAt>
-__device__ double2 fold_G(QAt qat, int L, int J, int s, int r)
+__device__ __forceinline__ double2 fold_G(QAt qat, int L, int J, int s, int r)
 {
-    double2 acc = make_double2(0.0, 0.0);
-    int t = 0;
-    for (int m = r; m <= L; m += J, ++t) {
-        double2 v = qat(m);
-        if (s & t & 1) { v.x = -v.x; v.y = -v.y; }
-        acc = cadd(acc, v);
+    double2 acc;
+    int mp, tt;                         // negative terms m = -mp, mp = tt J - r
+    if (r <= L) {
+        acc = qat(r);
+        int t = 1;
+        for (int m = r + J; m <= L; m += J, ++t) acc = cadd(acc, cneg_if(qat(m), s & t));
+        mp = J - r;
+        tt = 1;
+    } else {
+        mp = J - r;                     // r in (L, J): only negative terms
+        if (mp > L) return make_double2(0.0, 0.0);
+        acc = cneg_if(cconj_i(qat(mp)), s);
+        mp += J;
+        tt = 2;
     }
-    for (int tt = 1;; ++tt) {           // m = r - tt J < 0: q_m = conj(q_{-m})
-        const int mp = tt * J - r;
-        if (mp > L) break;
-        double2 v = cconj(qat(mp));
-        if (s & tt & 1) { v.x = -v.x; v.y = -v.y; }
-        acc = cadd(acc, v);
-    }
+    for (; mp <= L; mp += J, ++tt) acc = cadd(acc, cneg_if(cconj_i(qat(mp)), s & tt));
     return acc;
 }
 
@@ -166,12 +190,28 @@ __device__ __forceinline__ void bfly_fma(double2 a, double2 b, double2 w, double
     d.y = fma(2.0, a.y, -s.y);
 }
 
-// one pass of radix R over N points in blocks of B; tw(t) = e^{2 pi i t / N}
+// one pass of radix R over Ntot points: back-to-back sequences of Nseq
+// points (Nseq a multiple of B), in blocks of B; tw(t) = e^{2 pi i t / Nseq}
 template <int R, bool INV, class TW>
-__device__ __forceinline__ void mx_pass(double2 *x, int N, int B, const TW &tw)
+__device__ __forceinline__ void mx_pass(double2 *x, int Ntot, int Nseq, int B, const TW &tw)
 {
-    const int Ns = B / R, step = N / B;
-    for (int t = threadIdx.x; t < N / R; t += blockDim.x) {
+    const int Ns = B / R, step = Nseq / B;
+    if constexpr (INV) {
+        if (Ns == 1) {
+            // the first pass of decimation in time: every twiddle is 1, so
+            // only the R-point DFT remains (16 adds for radix 4, not 24 FMAs)
+            for (int t = threadIdx.x; t < Ntot / R; t += blockDim.x) {
+                double2 a[R];
+#pragma unroll
+                for (int q = 0; q < R; ++q) a[q] = x[t * R + q];
+                dft_small<R, 1>(a);
+#pragma unroll
+                for (int q = 0; q < R; ++q) x[t * R + q] = a[q];
+            }
+            return;
+        }
+    }
+    for (int t = threadIdx.x; t < Ntot / R; t += blockDim.x) {
         const int j = t % Ns, base = (t - j) * R + j;
         double2 a[R];
 #pragma unroll
@@ -211,44 +251,63 @@ __device__ __forceinline__ void mx_pass(double2 *x, int N, int B, const TW &tw)
     }
 }
 
+// Rader pass context: the ring's prime tables, and shared-memory scratch
+// for its convolutions ((N / p) (p - 1) points after the N of the ring)
+struct RaderCtx {
+    const RaderInfo *ri;
+    const int *rad;
+    const int *ints;
+    const double2 *dbl;
+    double2 *scratch;
+};
+
+template <bool CONJ>
+__device__ void rader_pass(double2 *x, int N, const RaderCtx &c);
+
 // BIG: the radix-11 and radix-13 butterflies are compiled in (they need many
-// more registers; only lengths with those factors are run with BIG)
-template <bool INV, bool BIG, class TW>
-__device__ __forceinline__ void mx_pass_any(int r, double2 *x, int N, int B, const TW &tw)
+// more registers; only lengths with those factors are run with BIG); RADER:
+// a radix above 13 is a prime done by Rader's algorithm (BIG kernels only)
+template <bool INV, bool BIG, bool RADER, class TW>
+__device__ __forceinline__ void mx_pass_any(int r, double2 *x, int Ntot, int Nseq, int B, const TW &tw,
+                                            const RaderCtx *rc)
 {
     switch (r) {
-    case 4: mx_pass<4, INV>(x, N, B, tw); break;
-    case 2: mx_pass<2, INV>(x, N, B, tw); break;
-    case 3: mx_pass<3, INV>(x, N, B, tw); break;
-    case 5: mx_pass<5, INV>(x, N, B, tw); break;
-    case 7: mx_pass<7, INV>(x, N, B, tw); break;
+    case 4: mx_pass<4, INV>(x, Ntot, Nseq, B, tw); break;
+    case 2: mx_pass<2, INV>(x, Ntot, Nseq, B, tw); break;
+    case 3: mx_pass<3, INV>(x, Ntot, Nseq, B, tw); break;
+    case 5: mx_pass<5, INV>(x, Ntot, Nseq, B, tw); break;
+    case 7: mx_pass<7, INV>(x, Ntot, Nseq, B, tw); break;
     default:
         if constexpr (BIG) {
-            if (r == 11) mx_pass<11, INV>(x, N, B, tw);
-            else mx_pass<13, INV>(x, N, B, tw);
+            if (r == 11) mx_pass<11, INV>(x, Ntot, Nseq, B, tw);
+            else if (r == 13) mx_pass<13, INV>(x, Ntot, Nseq, B, tw);
+            else if constexpr (RADER) rader_pass<!INV>(x, Ntot, *rc);
         }
         break;
     }
 }
 
-// natural order in, position order out, exponent -1
-template <bool BIG, class TW>
-__device__ void fft_mx_dif(double2 *x, int N, const int *__restrict__ rl, const TW &tw)
+// natural order in, position order out, exponent -1; Ntot / Nseq
+// sequences of Nseq points transformed side by side
+template <bool BIG, bool RADER, class TW>
+__device__ void fft_mx_dif(double2 *x, int Ntot, int Nseq, const int *__restrict__ rl, const TW &tw,
+                           const RaderCtx *rc = nullptr)
 {
     const int n = rl[0];
-    int B = N;
+    int B = Nseq;
     for (int i = 0; i < n; ++i) {
         const int r = rl[1 + i];
         __syncthreads();
-        mx_pass_any<false, BIG>(r, x, N, B, tw);
+        mx_pass_any<false, BIG, RADER>(r, x, Ntot, Nseq, B, tw, rc);
         B /= r;
     }
     __syncthreads();
 }
 
 // position order in, natural order out, exponent +1 (unnormalised)
-template <bool BIG, class TW>
-__device__ void fft_mx_dit(double2 *x, int N, const int *__restrict__ rl, const TW &tw)
+template <bool BIG, bool RADER, class TW>
+__device__ void fft_mx_dit(double2 *x, int Ntot, int Nseq, const int *__restrict__ rl, const TW &tw,
+                           const RaderCtx *rc = nullptr)
 {
     const int n = rl[0];
     int B = 1;
@@ -256,13 +315,14 @@ __device__ void fft_mx_dit(double2 *x, int N, const int *__restrict__ rl, const 
         const int r = rl[1 + i];
         B *= r;
         __syncthreads();
-        mx_pass_any<true, BIG>(r, x, N, B, tw);
+        mx_pass_any<true, BIG, RADER>(r, x, Ntot, Nseq, B, tw, rc);
     }
     __syncthreads();
 }
 
 // ring transform kinds: direct mixed radix over 2, 3, 4, 5, 7; Bluestein
-// (7-smooth convolution length); direct with radix 11 or 13 among the radices
+// (7-smooth convolution length); direct with radix 11 or 13 among the
+// radices, or with one prime above 13 done by Rader's algorithm
 enum RingFft { kDirect = 0, kBluestein = 1, kDirectBig = 2 };
 
 // position of X_k in position order
@@ -303,49 +363,117 @@ struct TwTable {
 // of length M (smooth, >= 2K - 1) with the chirp filter, stored transformed
 // in position order and scaled by 1/M.  x must hold M entries.  T is the
 // ring's e^{i pi n/J} table (J = 2K): the chirp c_j = e^{i pi j^2 / K} is
-// the root of index 2 j^2 mod 2J.
-static __device__ void bluestein_mx(double2 *x, int K, int M, const double2 *__restrict__ T,
+// the root of index 2 j^2 mod 2J.  PRECHIRP = false: the input already
+// carries its chirp c_k (the synthesis fold weights include it).
+template <bool PRECHIRP>
+__device__ void bluestein_mx(double2 *x, int K, int M, const double2 *__restrict__ T,
                              const double2 *__restrict__ fb, const int *__restrict__ rl, const TwTable &tw)
 {
     const int J = 2 * K;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        if (k < K) x[k] = cmul(x[k], ring_root(T, J, 2LL * k * k));
-        else x[k] = make_double2(0.0, 0.0);
+        if (k >= K) x[k] = make_double2(0.0, 0.0);
+        else if (PRECHIRP) x[k] = cmul(x[k], ring_root32(T, J, 2 * k * k));
     }
-    fft_mx_dif<false>(x, M, rl, tw);
+    fft_mx_dif<false, false>(x, M, M, rl, tw);
     for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = cmul(x[k], __ldg(fb + k));
-    fft_mx_dit<false>(x, M, rl, tw);
-    for (int n = threadIdx.x; n < K; n += blockDim.x) x[n] = cmul(x[n], ring_root(T, J, 2LL * n * n));
+    fft_mx_dit<false, false>(x, M, M, rl, tw);
+    for (int n = threadIdx.x; n < K; n += blockDim.x) x[n] = cmul(x[n], ring_root32(T, J, 2 * n * n));
     __syncthreads();
 }
 
-// Pixels of one ring from its q_m (m = 0..L): fold (Eq. tau), pack the
-// Hermitian spectrum into a half-length complex FFT, transform, and write
-// f_{2n}, f_{2n+1} as the real and imaginary parts of z_n.  All threads of
-// the block take part; sm holds K (power of two) or M (Bluestein) entries.
+// Rader's algorithm for the p-point DFTs of one pass over N points (blocks
+// of p contiguous points, no twiddles: the pass is the first of decimation
+// in time, or the last of decimation in frequency).  With g a primitive
+// root mod p, y_{g^w} = a_0 + sum_v a_{g^{-v}} e^{2 pi i g^{w-v} / p}: a
+// cyclic convolution of alpha_v = a_{g^{-v}} with beta_t = e^{2 pi i g^t / p},
+// done as forward transform, product with the stored transform of beta
+// (scaled by 1/(p-1)), inverse transform, all of length p - 1 and side by
+// side for the N / p blocks in the scratch.  a_0 joins every output through
+// the product's zero frequency, and y_0 = a_0 + (sum of alpha) is that
+// frequency before the product.  Exponent +1; CONJ = true gives exponent -1
+// as conj(DFT(conj a)).  Barriers: the transform's passes sync before they
+// start and after they end; the caller syncs before the next pass.
+template <bool CONJ>
+__device__ void rader_pass(double2 *x, int N, const RaderCtx &c)
+{
+    const RaderInfo ri = *c.ri;
+    const int p = ri.p, n = ri.n, tot = (N / p) * n;
+    const int *__restrict__ ga = c.ints + ri.ga;
+    const int *__restrict__ gi = c.ints + ri.gi;
+    const double2 *__restrict__ G = c.dbl + ri.G;
+    const int *__restrict__ rl = c.rad + ri.rl;
+    const TwTable tw{c.dbl + ri.tw};
+    double2 *S = c.scratch;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int b = e / n, v = e - b * n;
+        const double2 a = x[b * p + __ldg(gi + v)];
+        S[e] = CONJ ? cconj_i(a) : a;
+    }
+    fft_mx_dif<true, false>(S, tot, n, rl, tw);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int b = e / n, v = e - b * n;
+        const double2 A = S[e];
+        double2 C = cmul(A, __ldg(G + v));
+        if (v == 0) {
+            const double2 a0 = CONJ ? cconj_i(x[b * p]) : x[b * p];
+            const double2 y0 = cadd(a0, A);
+            x[b * p] = CONJ ? cconj_i(y0) : y0;
+            C = cadd(C, a0);
+        }
+        S[e] = C;
+    }
+    fft_mx_dit<true, false>(S, tot, n, rl, tw);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int b = e / n, w = e - b * n;
+        const double2 y = S[e];
+        x[b * p + __ldg(ga + w)] = CONJ ? cconj_i(y) : y;
+    }
+}
+
+// The Rader context of a ring of a BIG kernel (nullptr for other rings):
+// its scratch follows the ring's K points in shared memory.
+__device__ __forceinline__ const RaderCtx *rader_ctx(const PlanView &v, int ring, int K, double2 *sm, RaderCtx &rc)
+{
+    const int ri = v.ring_rdr[ring];
+    if (ri < 0) return nullptr;
+    rc = RaderCtx{v.rdr + ri, v.rad, v.rdr_int, v.rdr_dbl, sm + K};
+    return &rc;
+}
+
+// Pixels of one ring from its q_m (m = 0..L): fold (Eq. tau) and pack the
+// Hermitian spectrum into a half-length complex FFT in one step,
+// Z_k = G_k A_k + G_{k+K} B_k (8 FP64 instructions per k; the plan's fold
+// weights A, B hold the phi_0 phase, the packing twiddle and, on Bluestein
+// rings, the chirp), transform, and write f_{2n}, f_{2n+1} as the real and
+// imaginary parts of z_n.  All threads of the block take part; sm holds K
+// (direct), K plus the Rader scratch, or M (Bluestein) entries.
 template <int KIND, class QAt>
 __device__ void phi_synth_ring_at(const PlanView &v, int ring, QAt qat, double *out_ring, double2 *sm)
 {
-    constexpr bool BLUE = KIND == kBluestein;
+    constexpr bool BLUE = KIND == kBluestein, BIG = KIND == kDirectBig;
     const int L = v.lmax;
     const int J = v.ring_J[ring], K = J / 2, s = v.ring_s[ring];
     const double2 *__restrict__ T = v.tw + v.ring_tw[ring];
+    const double2 *__restrict__ AB = v.ab + v.ring_ab[ring];
     const int *__restrict__ rl = v.rad + v.ring_rad[ring];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double2 g0 = fold_G(qat, L, J, s, k);
-        double2 g1 = fold_G(qat, L, J, s, k + K);
-        if (s) g1 = times_i(g1);                           // e^{i pi K s / J} = i^s
-        const double2 E = cadd(g0, g1), O = csub(g0, g1);
-        double2 Zk = cadd(E, times_i(cmul(ring_root(T, J, 2LL * k), O)));
-        if (s) Zk = cmul(Zk, ring_root(T, J, k));          // common factor e^{i pi k s / J}
-        if (BLUE) sm[k] = Zk;
-        else sm[fft_pos(k, K, rl)] = Zk;
+        const double2 G0 = fold_G(qat, L, J, s, k);
+        const double2 G1 = fold_G(qat, L, J, s, k + K);
+        const double2 A = __ldg(AB + 2 * k), B = __ldg(AB + 2 * k + 1);
+        double2 Z;
+        Z.x = fma(G0.x, A.x, fma(-G0.y, A.y, fma(G1.x, B.x, -(G1.y * B.y))));
+        Z.y = fma(G0.x, A.y, fma(G0.y, A.x, fma(G1.x, B.y, G1.y * B.x)));
+        if (BLUE) sm[k] = Z;
+        else sm[fft_pos(k, K, rl)] = Z;
     }
     if constexpr (BLUE) {
         __syncthreads();
-        bluestein_mx(sm, K, v.ring_mx[ring], T, v.mfb + v.ring_mfb[ring], rl, TwTable{v.mtw + v.ring_mtw[ring]});
+        bluestein_mx<false>(sm, K, v.ring_mx[ring], T, v.mfb + v.ring_mfb[ring], rl,
+                            TwTable{v.mtw + v.ring_mtw[ring]});
     } else {
-        fft_mx_dit<KIND == kDirectBig>(sm, K, rl, TwRing{T, J});
+        RaderCtx rc;
+        const RaderCtx *rcp = BIG ? rader_ctx(v, ring, K, sm, rc) : nullptr;
+        fft_mx_dit<BIG, BIG>(sm, K, K, rl, TwRing{T, J}, rcp);
     }
     double2 *out = reinterpret_cast<double2 *>(out_ring);
     for (int n = threadIdx.x; n < K; n += blockDim.x) out[n] = sm[n];
@@ -375,8 +503,7 @@ __device__ void phi_synth_ring_qt(const PlanView &v, int ring, const double2 *qt
     auto qat = [=](int m) {
         const double2 x0 = ldq<CG>(q0 + m);
         if (m + 1 > L) return x0;
-        const double2 x1 = ldq<CG>(q1 + m);
-        return north ? make_double2(x0.x + x1.x, x0.y + x1.y) : make_double2(x0.x - x1.x, x0.y - x1.y);
+        return cadd(x0, cneg_if(ldq<CG>(q1 + m), !north));
     };
     phi_synth_ring_at<KIND>(v, ring, qat, out_ring, sm);
 }

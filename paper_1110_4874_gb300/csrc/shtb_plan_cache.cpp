@@ -23,7 +23,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'S', 'H', 'T', 'B', 'P', 'L', 'A', 'N'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 
 struct Header {
     char magic[8];
@@ -104,6 +104,8 @@ std::vector<const void **> pointer_fields(shtb_plan_s *p)
         (const void **)&v.ring_rad, (const void **)&v.rad, (const void **)&v.ring_mx,
         (const void **)&v.ring_mfb, (const void **)&v.mfb, (const void **)&v.ring_mtw, (const void **)&v.mtw,
         (const void **)&v.ring_M, (const void **)&v.ring_fb, (const void **)&v.fb, (const void **)&v.W,
+        (const void **)&v.ring_ab, (const void **)&v.ab, (const void **)&v.ring_rdr, (const void **)&v.rdr,
+        (const void **)&v.rdr_int, (const void **)&v.rdr_dbl,
         (const void **)&p->d_direct_rings, (const void **)&p->d_blue_rings, (const void **)&p->d_big_rings,
         (const void **)&p->d_chunk_list};
     if (p->bf) {

@@ -11,6 +11,7 @@
 #include <complex>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -281,6 +282,54 @@ bool radix_list(long long n, std::vector<int> &rl)
     for (int pr : {3, 5, 7, 11, 13})
         while (n % pr == 0) { n /= pr; rl.push_back(pr); }
     return n == 1;
+}
+
+bool is_prime(long long n)
+{
+    if (n < 2) return false;
+    for (long long d = 2; d * d <= n; ++d)
+        if (n % d == 0) return false;
+    return true;
+}
+
+// The prime p of Rader's algorithm for a transform of length K, or 0: K is
+// p times a product of 2, 3, 5, 7, 11, 13 with p > 13 prime (once), and
+// p - 1 factors over 2, 3, 5, 7, 11, 13, so that the cyclic convolution of
+// length p - 1 is itself a mixed-radix transform.
+long long rader_prime(long long K)
+{
+    long long n = K;
+    for (int pr : {2, 3, 5, 7, 11, 13})
+        while (n % pr == 0) n /= pr;
+    std::vector<int> rl;
+    if (n <= 13 || !is_prime(n) || !radix_list(n - 1, rl)) return 0;
+    return n;
+}
+
+// smallest primitive root modulo the prime p
+long long primitive_root(long long p)
+{
+    std::vector<long long> f;
+    long long n = p - 1;
+    for (long long d = 2; d * d <= n; ++d)
+        if (n % d == 0) {
+            f.push_back(d);
+            while (n % d == 0) n /= d;
+        }
+    if (n > 1) f.push_back(n);
+    auto powmod = [p](long long b, long long e) {
+        long long r = 1;
+        b %= p;
+        for (; e; e >>= 1, b = b * b % p)
+            if (e & 1) r = r * b % p;
+        return r;
+    };
+    for (long long g = 2;; ++g) {
+        bool ok = true;
+        for (long long q : f)
+            if (powmod(g, (p - 1) / q) == 1) { ok = false; break; }
+        if (ok) return g;
+    }
 }
 
 // smallest 7-smooth integer >= n
@@ -653,6 +702,11 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     std::vector<int> rad, ring_rad(p->nrings), ring_mx(p->nrings, 0), chunk_list;
     std::vector<long long> ring_mfb(p->nrings, 0), ring_mtw(p->nrings, 0);
     std::vector<double2> mfb, mtw;
+    std::vector<int> ring_rdr(p->nrings, -1), ring_smem(p->nrings, 0), rdr_int;
+    std::vector<RaderInfo> rdr;
+    std::vector<double2> rdr_dbl;
+    std::vector<long long> ring_ab(p->nrings, 0);
+    std::vector<double2> ab;
     {
         std::map<long long, int> rad_of_len;
         std::map<long long, long long> mtw_of_len;
@@ -675,18 +729,80 @@ int shtb_build_dense_plan(shtb_plan_s *p)
         p->max_K_direct = 0;
         p->max_M_mx = 0;
         p->max_K_big = 0;
+        // Rader primes: per prime p its tables (generator powers, the
+        // transformed convolution kernel, the length-(p-1) roots)
+        std::map<long long, int> rdr_of_p;
+        auto rader_off = [&](long long pr) {
+            auto it = rdr_of_p.find(pr);
+            if (it != rdr_of_p.end()) return it->second;
+            RaderInfo ri{};
+            ri.p = (int)pr;
+            ri.n = (int)(pr - 1);
+            ri.rl = radix_off(pr - 1);
+            const long long g = primitive_root(pr);
+            ri.ga = (int)rdr_int.size();
+            std::vector<long long> gp(pr - 1);
+            long long x = 1;
+            for (long long v = 0; v < pr - 1; ++v, x = x * g % pr) gp[v] = x;
+            for (long long v = 0; v < pr - 1; ++v) rdr_int.push_back((int)gp[v]);
+            ri.gi = (int)rdr_int.size();
+            for (long long v = 0; v < pr - 1; ++v) rdr_int.push_back((int)gp[(pr - 1 - v) % (pr - 1)]);
+            // beta_t = e^{2 pi i g^t / p}, DIF-transformed (exponent -1,
+            // position order) and scaled by 1/(p-1)
+            std::vector<std::complex<double>> beta(pr - 1);
+            for (long long t = 0; t < pr - 1; ++t) {
+                double c, sn;
+                sincospi_frac(2 * gp[t], pr, &c, &sn);
+                beta[t] = {c, sn};
+            }
+            std::vector<int> rl;
+            radix_list(pr - 1, rl);
+            mixed_dif_forward(beta, rl);
+            ri.G = (long long)rdr_dbl.size();
+            for (long long t = 0; t < pr - 1; ++t)
+                rdr_dbl.push_back(make_double2(beta[t].real() / (double)(pr - 1), beta[t].imag() / (double)(pr - 1)));
+            ri.tw = (long long)rdr_dbl.size();
+            for (long long t = 0; t < pr - 1; ++t) {
+                double c, sn;
+                sincospi_frac(2 * t, pr - 1, &c, &sn);
+                rdr_dbl.push_back(make_double2(c, sn));
+            }
+            rdr.push_back(ri);
+            return rdr_of_p[pr] = (int)rdr.size() - 1;
+        };
         for (int r = 0; r < p->nrings; ++r) {
             const long long K = p->ring_J[r] / 2;
             std::vector<int> rl;
-            if (radix_list(K, rl)) {
+            const long long pr = radix_list(K, rl) ? 0 : rader_prime(K);
+            if (pr) {
+                // mixed radix over the smooth part, the Rader pass last in the
+                // list (so first, untwiddled, in the synthesis transform)
+                auto it = rad_of_len.find(K);
+                if (it == rad_of_len.end()) {
+                    radix_list(K / pr, rl);
+                    rl.push_back((int)pr);
+                    const int off = (int)rad.size();
+                    rad.push_back((int)rl.size());
+                    rad.insert(rad.end(), rl.begin(), rl.end());
+                    it = rad_of_len.emplace(K, off).first;
+                }
+                ring_rad[r] = it->second;
+                ring_rdr[r] = rader_off(pr);
+                p->big_rings.push_back(r);
+                const long long entries = K + (K / pr) * (pr - 1);
+                ring_smem[r] = (int)entries;
+                p->max_K_big = std::max<int>(p->max_K_big, (int)entries);
+            } else if (radix_list(K, rl)) {
                 ring_rad[r] = radix_off(K);
                 const bool big = std::any_of(rl.begin(), rl.end(), [](int x) { return x > 7; });
                 (big ? p->big_rings : p->direct_rings).push_back(r);
                 int &mx = big ? p->max_K_big : p->max_K_direct;
                 mx = std::max<int>(mx, (int)K);
+                ring_smem[r] = (int)K;
             } else {
                 const long long M = smooth_at_least(2 * K - 1);
                 ring_mx[r] = (int)M;
+                ring_smem[r] = (int)M;
                 ring_rad[r] = radix_off(M);
                 p->blue_rings.push_back(r);
                 p->max_M_mx = std::max<long long>(p->max_M_mx, M);
@@ -734,11 +850,43 @@ int shtb_build_dense_plan(shtb_plan_s *p)
                 mfb[off[d] + k] = make_double2(bv[k].real() / M, bv[k].imag() / M);
         });
         for (int r : p->blue_rings) ring_mfb[r] = mfb_of_J[p->ring_J[r]];
+        // Fold weights per distinct (J, s, Bluestein or not): with
+        // G_r = sum_{m = r mod J, |m| <= L} (-1)^{s t} q_m (m = r + tJ),
+        // g_r = e^{i pi r s / J} G_r, and Z_k = E_k + i e^{2 pi i k/J} O_k,
+        // E, O = g_k +- g_{k+K}, one finds Z_k = G_k A_k + G_{k+K} B_k with
+        //   A_k = e^{i pi a/J} + i e^{i pi b/J},  B_k = i^s (e^{i pi a/J} - i e^{i pi b/J}),
+        //   a = k s, b = k (s + 2), both + 2 k^2 on Bluestein rings (the
+        // chirp e^{i pi k^2 / K} of the convolution's input).  Each
+        // exponential comes from an exact integer argument, so A and B are
+        // within one rounding of exact.
+        {
+            std::map<std::tuple<int, int, int>, long long> ab_of;
+            for (int r = 0; r < p->nrings; ++r) {
+                const int J = p->ring_J[r], sr = p->ring_s[r], blue = ring_mx[r] ? 1 : 0;
+                const auto key = std::make_tuple(J, sr, blue);
+                auto it = ab_of.find(key);
+                if (it == ab_of.end()) {
+                    const long long off = (long long)ab.size();
+                    const long long K = J / 2;
+                    ab.resize(ab.size() + 2 * K);
+                    for (long long k = 0; k < K; ++k) {
+                        const long long ch = blue ? (2 * k * k) % (2LL * J) : 0;
+                        double c1, s1, c2, s2;
+                        sincospi_frac(k * sr + ch, J, &c1, &s1);
+                        sincospi_frac(k * (sr + 2) + ch, J, &c2, &s2);
+                        ab[off + 2 * k] = make_double2(c1 - s2, s1 + c2);
+                        ab[off + 2 * k + 1] = sr ? make_double2(c2 - s1, c1 + s2) : make_double2(c1 + s2, s1 - c2);
+                    }
+                    it = ab_of.emplace(key, off).first;
+                }
+                ring_ab[r] = it->second;
+            }
+        }
         // heaviest rings first
         std::stable_sort(p->direct_rings.begin(), p->direct_rings.end(),
                          [&](int a, int b) { return p->ring_J[a] > p->ring_J[b]; });
         std::stable_sort(p->big_rings.begin(), p->big_rings.end(),
-                         [&](int a, int b) { return p->ring_J[a] > p->ring_J[b]; });
+                         [&](int a, int b) { return ring_smem[a] > ring_smem[b]; });
         std::stable_sort(p->blue_rings.begin(), p->blue_rings.end(),
                          [&](int a, int b) { return ring_mx[a] > ring_mx[b]; });
         constexpr int kSmallM = shtb_plan_s::kBlueSmallM;
@@ -771,7 +919,7 @@ int shtb_build_dense_plan(shtb_plan_s *p)
                 for (int r : *lists[k])
                     if (chunk_of[r] == cc) {
                         chunk_list.push_back(r);
-                        const int len = k == 1 ? ring_mx[r] : p->ring_J[r] / 2;
+                        const int len = ring_smem[r];
                         ck.len = std::max(ck.len, len);
                         if (k == 1 && len <= kSmallM) ck.len_small = std::max(ck.len_small, len);
                         else ++ck.split;              // lists are sorted longest first
@@ -824,6 +972,15 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     UP(ring_fb, ring_fb);
     UP(fb, fb);
     UP(W, W);
+    UP(ring_ab, ring_ab);
+    UP(ab, ab);
+    UP(ring_rdr, ring_rdr);
+    if (rdr.empty()) rdr.push_back(RaderInfo{});          // non-empty uploads
+    if (rdr_int.empty()) rdr_int.push_back(0);
+    if (rdr_dbl.empty()) rdr_dbl.push_back(make_double2(0.0, 0.0));
+    UP(rdr, rdr);
+    UP(rdr_int, rdr_int);
+    UP(rdr_dbl, rdr_dbl);
 #undef UP
     void *d;
     rc = plan_alloc_upload(p, &d, p->direct_rings.data(), sizeof(int) * p->direct_rings.size());
