@@ -103,6 +103,69 @@ __device__ __forceinline__ void bf_r_dispatch(int nr, const BfRItem &it, int L, 
     bf_r_pass<NB, NR, CG>(it, L, nhalf, ints, R, a0, astride, s0, sl, c, ubuf, qt);
 }
 
+// Few maps (C = 2 NB <= 4): a lane owns every component of its columns, so
+// one load of R[j][s] feeds C FMAs; the 32 lanes split the columns and each
+// column's sum runs over the rows in order, as with more maps (results do not
+// depend on how maps are grouped).  The row's C values of a are NB double2
+// loads shared by the warp.
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_r_pass_cl(const BfRItem &it, int L, int nhalf, const int *__restrict__ ints,
+                                             const double *__restrict__ R, const double2 *a0, int astride,
+                                             int s0, int lane, double *ubuf, double *qt)
+{
+    constexpr int C = 2 * NB;
+    double acc[NR][C];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] = 0.0;
+    const int k = it.k;
+#pragma unroll 4
+    for (int j = 0; j < it.nrows; ++j) {
+        double2 a[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) a[b] = CG ? __ldcg(a0 + (size_t)j * astride + b) : __ldg(a0 + (size_t)j * astride + b);
+        const double *__restrict__ Rj = R + (size_t)j * k + s0 + lane;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const double t = s0 + lane + 32 * r < k ? Rj[32 * r] : 0.0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                acc[r][2 * b] = fma(t, a[b].x, acc[r][2 * b]);
+                acc[r][2 * b + 1] = fma(t, a[b].y, acc[r][2 * b + 1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int sidx = s0 + lane + 32 * r;
+        if (sidx >= k) continue;
+        if (it.to_rings) {
+            const long long e = ints[it.out_off + sidx];
+#pragma unroll
+            for (int c = 0; c < C; ++c) qt_store(qt, e, nhalf, L, c, acc[r][c]);
+        } else {
+            double *dst = ubuf + (size_t)(it.out_off + sidx) * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) dst[c] = acc[r][c];
+        }
+    }
+}
+
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_r_dispatch_cl(int nr, const BfRItem &it, int L, int nhalf, const int *ints,
+                                                 const double *R, const double2 *a0, int astride, int s0,
+                                                 int lane, double *ubuf, double *qt)
+{
+    if constexpr (NR > 1) {
+        if (nr < NR) {
+            bf_r_dispatch_cl<NB, NR - 1, CG>(nr, it, L, nhalf, ints, R, a0, astride, s0, lane, ubuf, qt);
+            return;
+        }
+    }
+    bf_r_pass_cl<NB, NR, CG>(it, L, nhalf, ints, R, a0, astride, s0, lane, ubuf, qt);
+}
+
 // u = R^T a over one residual block.  ai: [idx][nmaps] complex, the group's
 // maps at b0 .. b0+NB-1; chain row j of (m, t) is a_{m+t+2j}.  A pass covers
 // up to LD x NRMAX columns; its per-lane column count is exact (the block's
@@ -115,6 +178,15 @@ __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, int nhalf, c
     constexpr int C = 2 * NB, LD = Lanes<C>::LD;
     const double *__restrict__ R = dbl + it.data_off;
     const long long aoff = alm_off(L, it.m) + it.t;   // chain row j at aoff + 2j
+    if constexpr (NB <= 2) {
+        constexpr int NRMAX = 4;
+        const double2 *a0 = ai + (size_t)(aoff + 2 * it.j0) * nmaps + b0;
+        for (int s0 = 0; s0 < it.k; s0 += 32 * NRMAX) {
+            const int nr = min(NRMAX, (it.k - s0 + 31) / 32);
+            bf_r_dispatch_cl<NB, NRMAX, CG>(nr, it, L, nhalf, ints, R, a0, 2 * nmaps, s0, lane, ubuf, qt);
+        }
+        return;
+    }
     const int sl = lane % LD, c = lane / LD;
     const double *a0 = reinterpret_cast<const double *>(ai + (size_t)(aoff + 2 * it.j0) * nmaps + b0) + c;
     const int astride = 4 * nmaps;                    // doubles between chain rows j and j + 1
@@ -140,17 +212,15 @@ __host__ __device__ constexpr int out_stride()
 template <int NB, int NR, bool CG>
 __device__ __forceinline__ void bf_dense_pass(int k, int nd, const double *__restrict__ T,
                                               const int *__restrict__ dpos, const double *uc, int q0, int dl,
-                                              int c, double *out)
+                                              int c, double *out, bool second)
 {
     constexpr int C = 2 * NB, LD = Lanes<C>::LD, OS = out_stride<C>();
-    // each row's dot product starts from its scratch entry (0, or the other
-    // child's contribution), so no separate add is needed afterwards
+    // every dot product starts from zero; the first child's rows are then
+    // stored, the second child's added to what the first child left (one
+    // order for every map-group width, see bf_level_item_pair)
     double acc[NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const int d = q0 + dl + r * LD;
-        acc[r] = d < nd ? out[dpos[d] * OS + c] : 0.0;
-    }
+    for (int r = 0; r < NR; ++r) acc[r] = 0.0;
     const double *__restrict__ Tq = T + q0 + dl;
 #pragma unroll 2
     for (int i = 0; i < k; ++i) {
@@ -165,21 +235,105 @@ __device__ __forceinline__ void bf_dense_pass(int k, int nd, const double *__res
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int d = q0 + dl + r * LD;
-        if (d < nd) out[dpos[d] * OS + c] = acc[r];
+        if (d < nd) {
+            double *o = out + dpos[d] * OS + c;
+            *o = second ? *o + acc[r] : acc[r];
+        }
     }
 }
 
 template <int NB, int NR, bool CG>
 __device__ __forceinline__ void bf_dense_dispatch(int nr, int k, int nd, const double *T, const int *dpos,
-                                                  const double *uc, int q0, int dl, int c, double *out)
+                                                  const double *uc, int q0, int dl, int c, double *out,
+                                                  bool second)
 {
     if constexpr (NR > 1) {
         if (nr < NR) {
-            bf_dense_dispatch<NB, NR - 1, CG>(nr, k, nd, T, dpos, uc, q0, dl, c, out);
+            bf_dense_dispatch<NB, NR - 1, CG>(nr, k, nd, T, dpos, uc, q0, dl, c, out, second);
             return;
         }
     }
-    bf_dense_pass<NB, NR, CG>(k, nd, T, dpos, uc, q0, dl, c, out);
+    bf_dense_pass<NB, NR, CG>(k, nd, T, dpos, uc, q0, dl, c, out, second);
+}
+
+// Few maps (C = 2 NB <= 4): the two children run side by side, lanes 16 h
+// to 16 h + 15 on child h, each lane owning every component of its dense
+// rows d = dl + 16 r (r < NR; nd < 128 = 16 x 8, so one pass), so one load
+// of T[i][d] feeds C FMAs.  Each row's dot product runs over i in order from
+// zero, as in bf_dense_pass; the first child's rows and identity entries are
+// stored, then the second child's are added: the same arithmetic as with
+// more maps, bit for bit.
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_pair_rows(const BfItem &it, const int *__restrict__ ints,
+                                             const double *__restrict__ dbl, const double *uin, double *out,
+                                             int lane)
+{
+    constexpr int C = 2 * NB, OS = out_stride<C>();
+    const int h = lane >> 4, dl = lane & 15;
+    const int k = it.k[h], nd = it.nd[h];
+    const int kmax = max(it.nd[0], it.nd[1]) ? max(it.k[0], it.k[1]) : 0;
+    const double2 *u2 = reinterpret_cast<const double2 *>(uin + (size_t)it.u_off[h] * C);
+    const double *__restrict__ Tq = dbl + it.T_off[h] + dl;
+    const int *__restrict__ dpos = ints + it.dpos_off[h];
+    double acc[NR][C];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] = 0.0;
+#pragma unroll 2
+    for (int i = 0; i < kmax; ++i) {
+        if (i < k) {
+            double2 uv[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) uv[b] = CG ? __ldcg(u2 + (size_t)i * NB + b) : __ldg(u2 + (size_t)i * NB + b);
+            const double *__restrict__ Ti = Tq + (size_t)i * nd;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const double t = dl + 16 * r < nd ? Ti[16 * r] : 0.0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    acc[r][2 * b] = fma(t, uv[b].x, acc[r][2 * b]);
+                    acc[r][2 * b + 1] = fma(t, uv[b].y, acc[r][2 * b + 1]);
+                }
+            }
+        }
+    }
+    for (int s = 0; s < 2; ++s) {
+        if (h == s) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int d = dl + 16 * r;
+                if (d < nd) {
+                    double *o = out + dpos[d] * OS;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) o[c] = s ? o[c] + acc[r][c] : acc[r][c];
+                }
+            }
+        }
+        // identity entries of child s: a store for the first child, an add
+        // for the second
+        const double *us = uin + (size_t)it.u_off[s] * C;
+        const int *__restrict__ ipos = ints + it.ipos_off[s];
+        for (int x = lane; x < it.k[s] * C; x += 32) {
+            const int i = x / C, cc = x - i * C;
+            double *o = out + ipos[i] * OS + cc;
+            *o = s ? *o + ldp<CG>(us + x) : ldp<CG>(us + x);
+        }
+        __syncwarp();
+    }
+}
+
+template <int NB, int NR, bool CG>
+__device__ __forceinline__ void bf_pair_dispatch(int nr, const BfItem &it, const int *ints, const double *dbl,
+                                                 const double *uin, double *out, int lane)
+{
+    if constexpr (NR > 1) {
+        if (nr < NR) {
+            bf_pair_dispatch<NB, NR - 1, CG>(nr, it, ints, dbl, uin, out, lane);
+            return;
+        }
+    }
+    bf_pair_rows<NB, NR, CG>(it, ints, dbl, uin, out, lane);
 }
 
 // Each child in turn: its dense rows (passes of up to LD x NRMAX rows, the
@@ -197,15 +351,20 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf
     for (int i = lane; i < it.nc * OS; i += 32) out[i] = 0.0;
     __syncwarp();
     const int dl = lane % LD, c = lane / LD;
+    if constexpr (NB <= 2) {
+        const int nr = (max(it.nd[0], it.nd[1]) + 15) / 16;      // <= 8: nd < kMaxCand
+        bf_pair_dispatch<NB, 8, CG>(max(nr, 1), it, ints, dbl, uin, out, lane);
+    }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
+        if constexpr (NB <= 2) break;
         const int k = it.k[s], nd = it.nd[s];
         const double *u = uin + (size_t)it.u_off[s] * C;
         const double *__restrict__ T = dbl + it.T_off[s];
         const int *__restrict__ dpos = ints + it.dpos_off[s];
         for (int q0 = 0; q0 < nd; q0 += LD * NRMAX) {
             const int nr = min(NRMAX, (nd - q0 + LD - 1) / LD);
-            bf_dense_dispatch<NB, NRMAX, CG>(nr, k, nd, T, dpos, u + c, q0, dl, c, out);
+            bf_dense_dispatch<NB, NRMAX, CG>(nr, k, nd, T, dpos, u + c, q0, dl, c, out, s == 1);
         }
         // identity entries: the first child's land on zeroed scratch (a store),
         // the second child's on whatever the first child left there
