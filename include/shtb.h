@@ -489,6 +489,25 @@ int shtb_test_host_butterfly(int nside, int lmax, double eps, int m, int t, int 
                              const double *a, double *q_out, double *q_exact, long long *info);
 
 /*
+ * Host-only measurement of the interpolation variant of the Legendre stage
+ * (Sec. 3.4 "Notes on interpolation", Eq. interpolation) for one chain
+ * (order m, parity t; rows l = m+t+2j, j < n): q is evaluated at the n
+ * positive roots z_i of P_{m+t+2n}^m and interpolated to the 2 nside
+ * half-rings by W(y, z_i) = P_{l*}(y) 2 z_i / (P'_{l*}(z_i) (y^2 - z_i^2)),
+ * l* = m+t+2n.  a: the chain's n coefficients (host); q_interp (2 nside
+ * doubles) receives the two-step result, q_exact the direct product
+ * Lambda^T a at the half-rings.  info[0..7] = {n, stored elements of Lambda
+ * at the roots compressed by the plan's butterfly builder, of W compressed
+ * by the same builder, of W compressed hierarchically (off-diagonal blocks
+ * by interpolative decomposition, the algebraic form of the FMM), of Lambda
+ * at the half-rings compressed by the butterfly builder, n * 2 nside,
+ * n^2 + n * 2 nside, depth of the half-rings' butterfly}.
+ * Errors: SHTB_EINVAL.
+ */
+int shtb_test_host_interp(int nside, int lmax, double eps, int m, int t, int leaf_cols, const double *a,
+                          double *q_interp, double *q_exact, long long *info);
+
+/*
  * Host-only check of the spin-weighted functions of spin plans (the
  * polarised transform, Sec. 5): s_lambda_lm(z_r) for s = +2 or -2 and
  * l = m..lmax at HEALPix half-ring r (0-based from the north pole), as the

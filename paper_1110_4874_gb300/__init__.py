@@ -125,6 +125,8 @@ SIGNATURES = {
     "shtb_test_host_butterfly": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "shtb_test_host_spin_column": (_I, [_I, _I, _I, _I, _I, _DP]),
+    "shtb_test_host_interp": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
+                                   ctypes.POINTER(ctypes.c_longlong)]),
     "shtb_struct_sizes": (_I, [ctypes.POINTER(_I)] * 4),
 }
 
@@ -476,6 +478,25 @@ def shtb_test_host_butterfly(nside: int, lmax: int, eps: float, m: int, t: int, 
                                           qe.ctypes.data_as(_DP), info),
            "shtb_test_host_butterfly")
     return q, qe, {"depth": info[0], "n_dense": info[1], "n_r": info[2], "n_ident": info[3]}
+
+
+def shtb_test_host_interp(nside: int, lmax: int, eps: float, m: int, t: int, a, leaf_cols: int = 32):
+    """The interpolation variant of one (m, parity) chain on the host: q at
+    the half-rings through the roots of P_{m+t+2n}^m and Eq. interpolation
+    (dense), the direct product, and the stored-element counts of both
+    routes under the plan's compression."""
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    Z = 2 * nside
+    q = np.zeros(Z)
+    qe = np.zeros(Z)
+    info = (ctypes.c_longlong * 8)()
+    _check(lib().shtb_test_host_interp(nside, lmax, float(eps), m, t, leaf_cols, a.ctypes.data_as(_DP),
+                                       q.ctypes.data_as(_DP), qe.ctypes.data_as(_DP), info),
+           "shtb_test_host_interp")
+    keys = ("n", "roots_butterfly", "interp_butterfly", "interp_hierarchical", "rings_butterfly",
+            "rings_dense", "two_step_dense", "rings_depth")
+    return q, qe, dict(zip(keys, list(info)))
 
 
 def shtb_test_host_spin_column(nside: int, lmax: int, m: int, s: int, r: int):

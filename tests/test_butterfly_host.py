@@ -145,3 +145,34 @@ def test_depth_zero_chains_are_the_dense_operator(nside, lmax):
                 assert info["n_dense"] == 0 and info["n_ident"] == 0
                 np.testing.assert_allclose(q, qe, rtol=0, atol=1e-15 * max(np.abs(qe).max(), 1e-300))
     assert seen > 0
+
+
+# ---------------------------------------------- interpolation variant (Sec. 3.4)
+@pytest.mark.parametrize("m,t", [(0, 0), (32, 1), (64, 0), (96, 1)])
+def test_interpolation_from_the_roots_reproduces_the_rings(m, t):
+    """Eq. interpolation: q at the roots of P_{m+t+2n}^m determines q at every
+    half-ring (the chain spans polynomials of degree < n in y^2)."""
+    nside, lmax = 64, 128
+    n = (lmax - m - t) // 2 + 1
+    a = np.random.default_rng(m + t).normal(size=n) / (m + t + 2 * np.arange(n) + 1)
+    q, qe, info = sh.shtb_test_host_interp(nside, lmax, 1e-10, m, t, a)
+    assert info["n"] == n
+    assert info["rings_dense"] == n * 2 * nside
+    assert info["two_step_dense"] == n * n + n * 2 * nside
+    assert np.linalg.norm(q - qe) <= 1e-11 * np.linalg.norm(qe)
+
+
+def test_interpolation_variant_stores_more_than_the_butterfly():
+    """The measured reason the interpolation variant is not built: Lambda at
+    the roots plus the interpolation matrix, each compressed as well as the
+    plan's builder (or a hierarchical FMM-style compression) can, hold more
+    elements -- so cost more FP64 FMAs per map -- than the butterfly of Lambda
+    at the HEALPix half-rings (Nside=256, L=512, eps=1e-10)."""
+    nside, lmax = 256, 512
+    for m in (0, 128, 256, 384):
+        for t in (0, 1):
+            n = (lmax - m - t) // 2 + 1
+            a = np.random.default_rng(m).normal(size=n)
+            _, _, info = sh.shtb_test_host_interp(nside, lmax, 1e-10, m, t, a)
+            two_step = info["roots_butterfly"] + min(info["interp_butterfly"], info["interp_hierarchical"])
+            assert two_step > info["rings_butterfly"], (m, t, info)
