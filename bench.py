@@ -478,13 +478,24 @@ def batched_serving(sh, synthetic, dev, reps=5):
     sh.shtb_batch_status(batch, stream)
     diff = max(float((m - w).abs().max() / w.abs().max()) for (_, _, m), w in zip(reqs, want))
     sh.shtb_batch_destroy(batch)
+    # each schedule family on its own: the one persistent launch (warps per
+    # block x work order) and the stage-kernel graph
+    families = {}
+    for name, kw in (("persistent_w4", dict(schedule=0, warps_per_block=4, lpt=True)),
+                     ("persistent_w8", dict(schedule=0, warps_per_block=8, lpt=True)),
+                     ("graph_4_streams", dict(schedule=1, streams=4))):
+        bb = sh.shtb_batch_create(reqs, autotune=False, **kw)
+        families[name] = round(event_ms(lambda: sh.shtb_batch_run(bb, stream), reps), 3)
+        sh.shtb_batch_status(bb, stream)
+        families[name + "_bitwise_equal"] = all(torch.equal(m, w) for (_, _, m), w in zip(reqs, want))
+        sh.shtb_batch_destroy(bb)
     for n in sizes[:-1]:
         plans[n].close()
     return ({"requests": 64, "maps": nmaps, "plans": len(sizes), "eps": 1e-10,
              "batched_ms": round(ms_batch, 3), "plain_ms": round(ms_plain, 3),
              "batched_over_plain": round(ms_plain / ms_batch, 3),
              "maps_per_s_batched": round(nmaps / (ms_batch * 1e-3), 1),
-             "max_rel_diff_vs_plain": diff, "schedule": info,
+             "max_rel_diff_vs_plain": diff, "schedule": info, "families_ms": families,
              "plan_build_s": round(build_s, 1), "create_and_tune_s": round(create_s, 1)},
             plans[sizes[-1]])
 

@@ -6,15 +6,21 @@
 // Requests that share a plan are merged along the map axis, so every stored
 // element of that plan's compressed operator is read once per group of up to
 // 8 maps (the paper's remark that many simultaneous transforms amortise the
-// precomputed data, Sec. 3.3).  The work of the whole batch is one list of
-// items in dependency order -- a_lm gather, residual blocks, each butterfly
-// level from the top down, parity combine, per-ring FFT -- grouped into packs
-// (a warp per item for the butterfly stages, a block per ring for the FFT).
-// Resident blocks claim packs in list order from a global counter; a pack of
-// stage s first waits until every item of stage s-1 is done.  Packs are
-// claimed in order and a claimed pack never waits on a later stage, so the
-// wait always ends; it is still bounded (spin_limit polls), after which the
-// kernel sets an error flag and returns, and the host reports SHTB_ETIMEOUT.
+// precomputed data, Sec. 3.3).  The persistent kernel runs the same item
+// bodies as the stand-alone stage kernels (shtb_bf_items.cuh,
+// shtb_phi_items.cuh), reading everything produced earlier in the launch
+// through L2 only, so every map it writes equals the single-request result
+// bit for bit.  The work of the whole batch is one list of items -- a_lm
+// gather (a warp per order m), residual blocks and butterfly levels (a warp
+// per item), ring transforms (a block per ring and map) -- cut into packs of
+// one map group's stage.  A pack first waits for the last non-empty earlier
+// stage of its own map group (the gather of its plan for the residual
+// blocks), so a small plan's rings can run while a large plan's levels are
+// still going.  Resident blocks claim packs from a global counter in phase
+// order (every dependency lies in an earlier phase), so a claimed pack only
+// ever waits on packs claimed before it and every wait ends; it is still
+// bounded (spin_limit polls), after which the kernel sets an error flag and
+// returns, and the host reports SHTB_ETIMEOUT.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,24 +29,28 @@
 #include <string>
 #include <vector>
 
-#include "shtb_batch_items.cuh"
+#include "shtb_bf_items.cuh"
 #include "shtb_butterfly.h"
 #include "shtb_internal.h"
+#include "shtb_phi_items.cuh"
 
 namespace {
 
-enum WorkType { W_GATHER = 0, W_RES = 1, W_LEVEL = 2, W_COMBINE = 3, W_PHI = 4 };
+enum WorkType { W_GATHER = 0, W_RES = 1, W_LEVEL = 2, W_PHI = 3 };
 
 struct BatchWork {
     int type;
     int g;        // plan group
-    int mg;       // map group (butterfly stages) or map (ring stage)
-    int idx;      // m, residual item, level item or ring
-    int level;
+    int mg;       // map group (index into the flat map-group table)
+    int idx;      // m (gather), residual item, level item or ring
+    int aux;      // level (W_LEVEL); map within the group (W_PHI)
+    int kind;     // ring transform kind (W_PHI)
 };
 
 struct BatchPack {
-    int stage, first, count, block;   // block = 1: one item for the whole block
+    int first, count, block;          // block = 1: one ring item for the whole block
+    int dep, need;                    // wait until counter dep reaches need (dep < 0: no wait)
+    int cnt;                          // counter the pack adds its item count to
 };
 
 struct BatchMG {                      // one map group of one plan group
@@ -56,7 +66,6 @@ struct BatchGroupDev {
     const double *dbl;
     const int *depth_parity;
     double2 *ai;                      // [nalm][nmaps]
-    double2 *q;                       // [nmaps][nrings][L+1]
     int nmaps;
     const double2 *const *alm_of_map; // request a_lm of each merged map
     double *const *map_of_map;        // request output map of each merged map
@@ -67,12 +76,11 @@ struct BatchDev {
     const BatchPack *packs;
     int npacks;
     const BatchGroupDev *groups;
-    const BatchMG *mgs;               // flat, mg index = group's mg_base + local
-    const int *mg_base;
-    const int *stage_total;
-    int *done;
-    int *next;
+    const BatchMG *mgs;
+    int *counters;                    // zeroed before every run
+    int *next;                        // pack claims
     int *err;
+    int scratch;                      // doubles of level-item scratch per warp
     long long spin_limit;
 };
 
@@ -80,30 +88,17 @@ template <int NB>
 __device__ void warp_item(const BatchDev &bd, const BatchWork &w, double *wsm, int lane)
 {
     const BatchGroupDev &G = bd.groups[w.g];
-    const BatchMG &M = bd.mgs[bd.mg_base[w.g] + w.mg];
-    switch (w.type) {
-    case W_RES: {
+    const BatchMG &M = bd.mgs[w.mg];
+    if (w.type == W_RES) {
         const BfRItem it = G.ritems[w.idx];
         double *ubuf = G.depth_parity[it.m * 2 + it.t] ? M.u1 : M.u0;
-        shtb_bdev::bf_r_item<NB, true>(it, G.v.lmax, G.ints, G.dbl, G.ai, G.nmaps, M.b0, ubuf, M.qt, lane);
-        break;
-    }
-    case W_LEVEL: {
-        const double *uin = (w.level % 2) ? M.u1 : M.u0;
-        double *uout = ((w.level - 1) % 2) ? M.u1 : M.u0;
-        shtb_bdev::bf_level_item<NB, true>(G.litems[w.level - 1][w.idx], G.ints, G.dbl, uin, uout, M.qt,
-                                          wsm, lane);
-        break;
-    }
-    case W_COMBINE: {
-        const size_t per_map = (size_t)G.v.nrings * (G.v.lmax + 1);
-        shtb_bdev::bf_combine_m<NB, true>(w.idx, G.v.lmax, G.v.nhalf, G.v.nrings, M.qt,
-                                         [&](int b) { return G.q + (size_t)(M.b0 + b) * per_map; }, lane,
-                                         32);
-        break;
-    }
-    default:
-        break;
+        shtb_dev::bf_r_item<NB, true>(it, G.v.lmax, G.v.nhalf, G.ints, G.dbl, G.ai, G.nmaps, M.b0, ubuf, M.qt,
+                                      lane);
+    } else {
+        const double *uin = (w.aux % 2) ? M.u1 : M.u0;
+        double *uout = ((w.aux - 1) % 2) ? M.u1 : M.u0;
+        shtb_dev::bf_level_item<NB, true>(G.litems[w.aux - 1][w.idx], G.v.lmax, G.v.nhalf, G.ints, G.dbl, uin,
+                                          uout, M.qt, wsm, lane);
     }
 }
 
@@ -112,7 +107,7 @@ __device__ void gather_item(const BatchDev &bd, const BatchWork &w, int lane)
 {
     const BatchGroupDev &G = bd.groups[w.g];
     const int m = w.idx, L = G.v.lmax;
-    const long long off = shtb_bdev::alm_off(L, m);
+    const long long off = shtb_dev::alm_off(L, m);
     const int n = L - m + 1;
     for (int i = lane; i < n * G.nmaps; i += 32) {
         const int b = i / n, dl = i - b * n;
@@ -122,7 +117,30 @@ __device__ void gather_item(const BatchDev &bd, const BatchWork &w, int lane)
     }
 }
 
-__global__ void __launch_bounds__(256) batch_kernel(BatchDev bd)
+// one ring of one map of a map group, by the whole block, from the group's
+// parity halves (fused combine, as in phi_synth_qt_kernel)
+__device__ void ring_item(const BatchDev &bd, const BatchWork &w, double2 *sm)
+{
+    const BatchGroupDev &G = bd.groups[w.g];
+    const BatchMG &M = bd.mgs[w.mg];
+    const double2 *qt = reinterpret_cast<const double2 *>(M.qt);
+    double *out = G.map_of_map[M.b0 + w.aux] + G.v.ring_start[w.idx];
+    switch (w.kind) {
+    case shtb_dev::kBluestein:
+        shtb_dev::phi_synth_ring_qt<shtb_dev::kBluestein, true>(G.v, w.idx, qt, w.aux, out, sm);
+        break;
+    case shtb_dev::kDirectBig:
+        shtb_dev::phi_synth_ring_qt<shtb_dev::kDirectBig, true>(G.v, w.idx, qt, w.aux, out, sm);
+        break;
+    default:
+        shtb_dev::phi_synth_ring_qt<shtb_dev::kDirect, true>(G.v, w.idx, qt, w.aux, out, sm);
+        break;
+    }
+}
+
+// at most 8 warps per block, two blocks per SM (128 registers a thread:
+// the radix-11/13 and Rader ring bodies need about that many)
+__global__ void __launch_bounds__(256, 2) batch_kernel(BatchDev bd)
 {
     extern __shared__ double bsm[];
     __shared__ int s_pack, s_abort;
@@ -136,9 +154,9 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchDev bd)
         const int pk = s_pack;
         if (pk >= bd.npacks) return;
         const BatchPack P = bd.packs[pk];
-        if (P.stage > 0 && threadIdx.x == 0) {
+        if (P.dep >= 0 && threadIdx.x == 0) {
             long long polls = 0;
-            while (atomicAdd(&bd.done[P.stage - 1], 0) < bd.stage_total[P.stage - 1]) {
+            while (atomicAdd(&bd.counters[P.dep], 0) < P.need) {
                 if (atomicAdd(bd.err, 0) != 0 || ++polls > bd.spin_limit) {
                     atomicExch(bd.err, 1);
                     s_abort = 1;
@@ -151,23 +169,14 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchDev bd)
         __syncthreads();
         if (s_abort) return;
         if (P.block) {
-            const BatchWork w = bd.work[P.first];
-            const BatchGroupDev &G = bd.groups[w.g];
-            const int ring = w.idx, b = w.mg;
-            const double2 *qr = G.q + ((size_t)b * G.v.nrings + ring) * (G.v.lmax + 1);
-            double *out = G.map_of_map[b] + G.v.ring_start[ring];
-            if (G.v.ring_M[ring] > 0)
-                shtb_bdev::phi_synth_ring<true, true>(G.v, ring, qr, out, reinterpret_cast<double2 *>(bsm));
-            else
-                shtb_bdev::phi_synth_ring<false, true>(G.v, ring, qr, out, reinterpret_cast<double2 *>(bsm));
+            ring_item(bd, bd.work[P.first], reinterpret_cast<double2 *>(bsm));
         } else if (wib < P.count) {
             const BatchWork w = bd.work[P.first + wib];
             if (w.type == W_GATHER) {
                 gather_item(bd, w, lane);
             } else {
-                const BatchMG &M = bd.mgs[bd.mg_base[w.g] + w.mg];
-                double *wsm = bsm + (size_t)wib * shtb::kMaxCand * 16;
-                switch (M.nb) {
+                double *wsm = bsm + (size_t)wib * bd.scratch;
+                switch (bd.mgs[w.mg].nb) {
                 case 8: warp_item<8>(bd, w, wsm, lane); break;
                 case 4: warp_item<4>(bd, w, wsm, lane); break;
                 case 2: warp_item<2>(bd, w, wsm, lane); break;
@@ -178,12 +187,11 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchDev bd)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(&bd.done[P.stage], P.count);
+            atomicAdd(&bd.counters[P.cnt], P.count);
         }
     }
 }
 
-size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
@@ -201,7 +209,9 @@ struct shtb_batch_s {
     std::vector<void *> allocs;
     // device tables of the current schedule
     BatchDev dev{};
-    int nstages = 0, warps = 4, grid = 0;
+    int ncounters = 0, warps = 4, grid = 0;
+    int stall_counter = -1;           // the gather counter shtb_test_batch_stall holds back
+    std::vector<char> host_packs;     // the uploaded pack table (BatchPack records)
     size_t smem = 0;
     std::vector<void *> sched_allocs;
     // stage-kernel schedule: per plan group the merged a_lm and pointer
@@ -252,15 +262,24 @@ void free_schedule(shtb_batch_s *b)
     b->sched_allocs.clear();
     b->gg.clear();
     b->dev = BatchDev{};
-    b->nstages = 0;
+    b->ncounters = 0;
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
 }
 
+// relative work of one ring transform (for the largest-first order)
+long long ring_cost(const shtb_plan_s *p, int kind, int r)
+{
+    const long long K = p->ring_J[r] / 2;
+    long long lg = 1;
+    while ((1LL << lg) < K) ++lg;
+    return kind == shtb_dev::kBluestein ? 8 * K * (lg + 1) : K * lg;
+}
+
 // Builds the work list, packs and device tables for `warps` warps per block
-// and map groups of at most `width` maps; work inside a stage in decreasing
+// and map groups of at most `width` maps; work inside a phase in decreasing
 // size (lpt = 1) or in plan order (lpt = 0).
 int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
 {
@@ -268,19 +287,28 @@ int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
     b->mode = 0;
     std::vector<BatchGroupDev> gdev(b->groups.size());
     std::vector<BatchMG> mgs;
-    std::vector<int> mg_base(b->groups.size());
-    std::vector<std::vector<BatchWork>> stages;
-    int dmax = 0;
-    for (auto &G : b->groups) dmax = std::max(dmax, G.plan->bf->depth_max);
-    const int S_GATHER = 0, S_RES = 1, S_COMB = 2 + dmax, S_PHI = 3 + dmax;
-    stages.resize(S_PHI + 1);
-    std::vector<std::vector<long long>> cost(stages.size());
-    size_t smem_fft = 0;
+    int dmax = 0, cmax = 2, maxnc = 1;
+    for (auto &G : b->groups) {
+        const BfPlanDev &bf = *G.plan->bf;
+        dmax = std::max(dmax, bf.depth_max);
+        for (int nc : bf.level_maxnc) maxnc = std::max(maxnc, nc);
+    }
+    // phases: gather 0, residual blocks 1, level l at 2 + (dmax - l), rings 2 + dmax
+    const int nphase = 3 + dmax;
+    struct Unit {                     // the items of one stage of one map group (or one plan's gather)
+        int phase, dep, need, cnt, block;
+        std::vector<BatchWork> items;
+        std::vector<long long> cost;
+    };
+    std::vector<Unit> units;
+    int ncounters = 0;
+    size_t ring_entries = 1;
     int rc;
     for (size_t g = 0; g < b->groups.size(); ++g) {
         auto &G = b->groups[g];
         shtb_plan_s *p = G.plan;
         const BfPlanDev &bf = *p->bf;
+        if (bf.depth_max > 16) return shtb_fail(SHTB_ENOTSUP, "butterfly deeper than the batch tables");
         BatchGroupDev &D = gdev[g];
         D.v = p->view;
         D.ritems = bf.ritems;
@@ -292,19 +320,41 @@ int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
         void *d;
         if ((rc = balloc(b->sched_allocs, &d, sizeof(double2) * (size_t)p->nalm * G.nmaps))) return rc;
         D.ai = (double2 *)d;
-        if ((rc = balloc(b->sched_allocs, &d, sizeof(double2) * (size_t)G.nmaps * p->nrings * (p->lmax + 1))))
-            return rc;
-        D.q = (double2 *)d;
         if ((rc = balloc(b->sched_allocs, &d, sizeof(void *) * G.nmaps, G.alm_of_map.data()))) return rc;
         D.alm_of_map = (const double2 *const *)d;
         if ((rc = balloc(b->sched_allocs, &d, sizeof(void *) * G.nmaps, G.map_of_map.data()))) return rc;
         D.map_of_map = (double *const *)d;
-        // map groups of power-of-two widths up to `width`
-        mg_base[g] = (int)mgs.size();
+        ring_entries = std::max<size_t>(ring_entries, (size_t)std::max({p->max_K_direct, p->max_M_mx, p->max_K_big}));
+        // ring transform kind of every ring, from the plan's ring lists
+        std::vector<int> kind(p->nrings, shtb_dev::kDirect);
+        for (int r : p->blue_rings) kind[r] = shtb_dev::kBluestein;
+        for (int r : p->big_rings) kind[r] = shtb_dev::kDirectBig;
+        // ---- gather of this plan group
+        Unit ug{0, -1, 0, ncounters++, 0, {}, {}};
+        const int gather_cnt = ug.cnt;
+        for (int m = 0; m <= p->lmax; ++m) {
+            ug.items.push_back({W_GATHER, (int)g, 0, m, 0, 0});
+            ug.cost.push_back((long long)(p->lmax - m + 1) * G.nmaps);
+        }
+        const int gather_total = (int)ug.items.size();
+        units.push_back(std::move(ug));
+        // host copies of the item lists, for the costs
+        std::vector<BfRItem> rh(bf.n_ritems);
+        if (bf.n_ritems)
+            SHTB_CUDA_TRY(cudaMemcpy(rh.data(), bf.ritems, sizeof(BfRItem) * bf.n_ritems, cudaMemcpyDeviceToHost));
+        std::vector<std::vector<BfItem>> lh(bf.depth_max);
+        for (int l = 1; l <= bf.depth_max; ++l) {
+            lh[l - 1].resize(bf.level_counts[l - 1]);
+            if (!lh[l - 1].empty())
+                SHTB_CUDA_TRY(cudaMemcpy(lh[l - 1].data(), bf.level_items[l - 1], sizeof(BfItem) * lh[l - 1].size(),
+                                         cudaMemcpyDeviceToHost));
+        }
+        // ---- map groups of power-of-two widths up to `width`
         for (int b0 = 0; b0 < G.nmaps;) {
             const int left = G.nmaps - b0;
             int nb = 1;
             while (nb * 2 <= std::min(left, width)) nb *= 2;
+            cmax = std::max(cmax, 2 * nb);
             BatchMG M{};
             M.b0 = b0;
             M.nb = nb;
@@ -315,84 +365,103 @@ int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
             M.u1 = (double *)d;
             if ((rc = balloc(b->sched_allocs, &d, entry * (size_t)bf.qt_entries))) return rc;
             M.qt = (double *)d;
+            const int mg = (int)mgs.size();
             mgs.push_back(M);
-            b0 += nb;
-        }
-        const int nmg2 = (int)mgs.size() - mg_base[g];
-        // ---- work
-        for (int m = 0; m <= p->lmax; ++m) {
-            stages[S_GATHER].push_back({W_GATHER, (int)g, 0, m, 0});
-            cost[S_GATHER].push_back((long long)(p->lmax - m + 1) * G.nmaps);
-        }
-        std::vector<BfRItem> rh(bf.n_ritems);
-        cudaMemcpy(rh.data(), bf.ritems, sizeof(BfRItem) * bf.n_ritems, cudaMemcpyDeviceToHost);
-        for (int mg = 0; mg < nmg2; ++mg) {
-            const int nb = mgs[mg_base[g] + mg].nb;
-            for (int i = 0; i < bf.n_ritems; ++i) {
-                stages[S_RES].push_back({W_RES, (int)g, mg, i, 0});
-                cost[S_RES].push_back((long long)rh[i].nrows * rh[i].k * nb);
+            // each stage waits for the last non-empty stage before it
+            int dep = gather_cnt, need = gather_total;
+            if (bf.n_ritems > 0) {
+                Unit u{1, dep, need, ncounters++, 0, {}, {}};
+                for (int i = 0; i < bf.n_ritems; ++i) {
+                    u.items.push_back({W_RES, (int)g, mg, i, 0, 0});
+                    u.cost.push_back((long long)rh[i].nrows * rh[i].k * nb);
+                }
+                dep = u.cnt;
+                need = (int)u.items.size();
+                units.push_back(std::move(u));
             }
             for (int l = bf.depth_max; l >= 1; --l) {
-                const int st = 2 + (dmax - l);
-                std::vector<BfItem> lh(bf.level_counts[l - 1]);
-                cudaMemcpy(lh.data(), bf.level_items[l - 1], sizeof(BfItem) * lh.size(), cudaMemcpyDeviceToHost);
-                for (size_t i = 0; i < lh.size(); ++i) {
-                    stages[st].push_back({W_LEVEL, (int)g, mg, (int)i, l});
-                    cost[st].push_back(((long long)lh[i].k[0] * lh[i].nd[0] + (long long)lh[i].k[1] * lh[i].nd[1] +
-                                        lh[i].nc) * nb);
+                if (lh[l - 1].empty()) continue;
+                Unit u{2 + (dmax - l), dep, need, ncounters++, 0, {}, {}};
+                for (size_t i = 0; i < lh[l - 1].size(); ++i) {
+                    const BfItem &it = lh[l - 1][i];
+                    u.items.push_back({W_LEVEL, (int)g, mg, (int)i, l, 0});
+                    u.cost.push_back(((long long)it.k[0] * it.nd[0] + (long long)it.k[1] * it.nd[1] + it.nc) * nb);
                 }
+                dep = u.cnt;
+                need = (int)u.items.size();
+                units.push_back(std::move(u));
             }
-            for (int m = 0; m <= p->lmax; ++m) {
-                stages[S_COMB].push_back({W_COMBINE, (int)g, mg, m, 0});
-                cost[S_COMB].push_back((long long)p->nhalf * nb);
-            }
+            Unit ur{2 + dmax, dep, need, ncounters++, 1, {}, {}};
+            for (int bl = 0; bl < nb; ++bl)
+                for (int r = 0; r < p->nrings; ++r) {
+                    ur.items.push_back({W_PHI, (int)g, mg, r, bl, kind[r]});
+                    ur.cost.push_back(ring_cost(p, kind[r], r));
+                }
+            units.push_back(std::move(ur));
+            b0 += nb;
         }
-        for (int mp = 0; mp < G.nmaps; ++mp)
-            for (int r = 0; r < p->nrings; ++r) {
-                stages[S_PHI].push_back({W_PHI, (int)g, mp, r, 0});
-                const long long K = p->ring_J[r] / 2, M = p->ring_M[r];
-                cost[S_PHI].push_back(M > 0 ? 3 * M : K);
-            }
-        smem_fft = std::max(smem_fft, sizeof(double2) * (size_t)std::max(p->max_K_pow2, p->max_M_blue));
     }
-    // ---- order, packs
+    // ---- packs in phase order; within a phase the heaviest work first
     std::vector<BatchWork> work;
     std::vector<BatchPack> packs;
-    std::vector<int> totals(stages.size(), 0);
-    for (size_t s = 0; s < stages.size(); ++s) {
-        std::vector<int> ord(stages[s].size());
-        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-        if (lpt) std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return cost[s][a] > cost[s][c]; });
-        const int first = (int)work.size();
-        for (int i : ord) work.push_back(stages[s][i]);
-        totals[s] = (int)ord.size();
-        const bool block = (int)s == S_PHI;
-        const int per = block ? 1 : warps;
-        for (int i = 0; i < (int)ord.size(); i += per)
-            packs.push_back({(int)s, first + i, std::min(per, (int)ord.size() - i), block ? 1 : 0});
+    std::vector<std::pair<long long, std::pair<int, int>>> order;   // (cost, (unit, first item))
+    for (int ph = 0; ph < nphase; ++ph) {
+        order.clear();
+        for (size_t u = 0; u < units.size(); ++u) {
+            Unit &U = units[u];
+            if (U.phase != ph) continue;
+            std::vector<int> ord(U.items.size());
+            for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+            if (lpt) std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return U.cost[a] > U.cost[c]; });
+            std::vector<BatchWork> it2;
+            std::vector<long long> c2;
+            for (int i : ord) {
+                it2.push_back(U.items[i]);
+                c2.push_back(U.cost[i]);
+            }
+            U.items.swap(it2);
+            U.cost.swap(c2);
+            const int per = U.block ? 1 : warps;
+            for (int i = 0; i < (int)U.items.size(); i += per) {
+                long long c = 0;
+                for (int k = i; k < std::min<int>(i + per, (int)U.items.size()); ++k) c += U.cost[k];
+                order.push_back({c, {(int)u, i}});
+            }
+        }
+        if (lpt) std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &c) { return a.first > c.first; });
+        for (auto &o : order) {
+            Unit &U = units[o.second.first];
+            const int i = o.second.second, per = U.block ? 1 : warps;
+            const int n = std::min(per, (int)U.items.size() - i);
+            packs.push_back({(int)work.size(), n, U.block, U.dep, U.need, U.cnt});
+            for (int k = i; k < i + n; ++k) work.push_back(U.items[k]);
+        }
     }
     void *d;
     if ((rc = balloc(b->sched_allocs, &d, sizeof(BatchWork) * work.size(), work.data()))) return rc;
     b->dev.work = (const BatchWork *)d;
     if ((rc = balloc(b->sched_allocs, &d, sizeof(BatchPack) * packs.size(), packs.data()))) return rc;
     b->dev.packs = (const BatchPack *)d;
+    b->host_packs.assign((const char *)packs.data(), (const char *)(packs.data() + packs.size()));
     b->dev.npacks = (int)packs.size();
     if ((rc = balloc(b->sched_allocs, &d, sizeof(BatchGroupDev) * gdev.size(), gdev.data()))) return rc;
     b->dev.groups = (const BatchGroupDev *)d;
     if ((rc = balloc(b->sched_allocs, &d, sizeof(BatchMG) * mgs.size(), mgs.data()))) return rc;
     b->dev.mgs = (const BatchMG *)d;
-    if ((rc = balloc(b->sched_allocs, &d, sizeof(int) * mg_base.size(), mg_base.data()))) return rc;
-    b->dev.mg_base = (const int *)d;
-    if ((rc = balloc(b->sched_allocs, &d, sizeof(int) * totals.size(), totals.data()))) return rc;
-    b->dev.stage_total = (const int *)d;
-    if ((rc = balloc(b->sched_allocs, &d, sizeof(int) * (totals.size() + 2)))) return rc;
-    b->dev.done = (int *)d;
-    b->dev.next = b->dev.done + totals.size();
-    b->dev.err = b->dev.done + totals.size() + 1;
+    if ((rc = balloc(b->sched_allocs, &d, sizeof(int) * (size_t)(ncounters + 2)))) return rc;
+    b->dev.counters = (int *)d;
+    b->dev.next = b->dev.counters + ncounters;
+    b->dev.err = b->dev.counters + ncounters + 1;
     b->dev.spin_limit = b->opts.spin_limit > 0 ? b->opts.spin_limit : 20000000LL;
-    b->nstages = (int)totals.size();
+    // level-item scratch per warp: the batch's longest candidate list x
+    // (C + 1) doubles for its widest map group (C = 2 x maps)
+    if (cmax > 16 || maxnc > shtb::kMaxCand) return shtb_fail(SHTB_EINVAL, "map group or candidate list too large");
+    b->dev.scratch = maxnc * (cmax + 1);
+    b->ncounters = ncounters;
+    b->stall_counter = 0;             // the first plan group's gather
     b->warps = warps;
-    b->smem = std::max(smem_fft, sizeof(double) * (size_t)warps * shtb::kMaxCand * 16);
+    b->smem = std::max(sizeof(double2) * ring_entries, sizeof(double) * (size_t)warps * b->dev.scratch);
+    if (b->smem > 227 * 1024) return shtb_fail(SHTB_ENOTSUP, "batch kernel shared memory above 227 KB");
     SHTB_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     int per_sm = 0, nsm = 0;
     SHTB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, 32 * warps, b->smem));
@@ -500,7 +569,7 @@ int enqueue_graph(shtb_batch_s *b, cudaStream_t st)
 int enqueue(shtb_batch_s *b, cudaStream_t st)
 {
     if (b->mode == 1) return enqueue_graph(b, st);
-    SHTB_CUDA_TRY(cudaMemsetAsync(b->dev.done, 0, sizeof(int) * (b->nstages + 2), st));
+    SHTB_CUDA_TRY(cudaMemsetAsync(b->dev.counters, 0, sizeof(int) * (b->ncounters + 2), st));
     batch_kernel<<<b->grid, 32 * b->warps, b->smem, st>>>(b->dev);
     SHTB_CUDA_TRY(cudaGetLastError());
     return SHTB_OK;
@@ -693,13 +762,15 @@ int shtb_batch_schedule(shtb_batch b, int *schedule, int *streams)
 int shtb_test_batch_stall(shtb_batch b, int on)
 {
     if (b && b->mode != 0) return shtb_fail(SHTB_ENOTSUP, "stage waits exist in the persistent schedule only");
-    if (!b || b->nstages < 2) return shtb_fail(SHTB_EINVAL, "batch is NULL or empty");
-    int t0 = 0;
-    SHTB_CUDA_TRY(cudaMemcpy(&t0, b->dev.stage_total, sizeof(int), cudaMemcpyDeviceToHost));
-    // one more item than stage 0 has: every later stage waits until its bound runs out
-    const int want = on ? t0 + 1 : t0 - 1;
-    if ((on && t0 < 0) || (!on && t0 < 1)) return shtb_fail(SHTB_EINVAL, "stall state");
-    SHTB_CUDA_TRY(cudaMemcpy((void *)b->dev.stage_total, &want, sizeof(int), cudaMemcpyHostToDevice));
+    if (!b || b->ncounters < 2 || b->stall_counter < 0) return shtb_fail(SHTB_EINVAL, "batch is NULL or empty");
+    // every pack waiting on the first plan group's gather waits for one item
+    // more than that gather has, so its wait runs out (on) or not (off)
+    std::vector<BatchPack> packs(b->host_packs.size() / sizeof(BatchPack));
+    memcpy(packs.data(), b->host_packs.data(), b->host_packs.size());
+    for (auto &P : packs)
+        if (P.dep == b->stall_counter) P.need += on ? 1 : 0;
+    SHTB_CUDA_TRY(cudaMemcpy((void *)b->dev.packs, packs.data(), sizeof(BatchPack) * packs.size(),
+                             cudaMemcpyHostToDevice));
     return SHTB_OK;
 }
 

@@ -1,6 +1,6 @@
 // Per-work-item device bodies of the butterfly synthesis (Sec. 3.2) used by
-// the stage kernels of shtb_butterfly.cu (the persistent batch kernel keeps
-// its own copies, shtb_batch_items.cuh).  CG = true reads data through L2
+// the stage kernels of shtb_butterfly.cu and by the persistent batch kernel
+// of shtb_batch.cu.  CG = true reads data through L2
 // only (ld.global.cg), for data produced earlier in the same launch: L1 is
 // not coherent between SMs within one launch.
 #pragma once

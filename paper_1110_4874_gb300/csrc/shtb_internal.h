@@ -103,14 +103,6 @@ struct PlanView {
     const double2 *mfb;
     const long long *ring_mtw;
     const double2 *mtw;
-    // radix-2 tables of the persistent batch kernel: Bluestein length
-    // (0 = power-of-two ring), filter offset in fb (bit-reversed order),
-    // e^{2 pi i n / Wlen}
-    const int *ring_M;
-    const long long *ring_fb;
-    const double2 *fb;
-    const double2 *W;
-    int Wlen;
     // fold weights of the synthesis ring kernels: ab + ring_ab[ring] holds,
     // for k < K = J/2, {A_k, B_k} with Z_k = G_k A_k + G_{k+K} B_k (G the
     // ring's folded spectrum without its phi_0 phase); the half-pixel phase,
@@ -140,7 +132,7 @@ struct shtb_plan_s {
     shtb_plan_opts opts{};
 
     // host copies of the ring description
-    std::vector<int> ring_J, ring_s, ring_M;
+    std::vector<int> ring_J, ring_s;
     std::vector<long long> ring_start;
 
     // ring lists of the three ring-kernel variants (mixed radix: direct
@@ -171,9 +163,6 @@ struct shtb_plan_s {
     int *d_chunk_list = nullptr;
     cudaStream_t copy_stream = nullptr;            // created on first use, owned
     cudaEvent_t chunk_ev[kPhiChunks] = {};
-    // largest radix-2 transform of the batch kernel (power-of-two K, or the
-    // power-of-two Bluestein length)
-    int max_K_pow2 = 0, max_M_blue = 0;
 
     // device allocations owned by the plan (freed in destroy), with their sizes
     std::vector<void *> allocations;

@@ -1,7 +1,7 @@
 // Device bodies of the ring stage (Eq. sh-baseline, Eq. tau): complex
 // helpers, the mixed-radix and Bluestein FFTs in shared memory and the
-// per-ring synthesis used by the ring kernels of shtb_phi.cu (the persistent
-// batch kernel keeps its own radix-2 copies, shtb_batch_items.cuh).
+// per-ring synthesis used by the ring kernels of shtb_phi.cu and by the
+// persistent batch kernel of shtb_batch.cu.
 #pragma once
 
 #include <cuda_runtime.h>

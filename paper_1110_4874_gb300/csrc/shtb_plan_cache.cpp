@@ -23,7 +23,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'S', 'H', 'T', 'B', 'P', 'L', 'A', 'N'};
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 4;
 
 struct Header {
     char magic[8];
@@ -103,7 +103,6 @@ std::vector<const void **> pointer_fields(shtb_plan_s *p)
         (const void **)&v.ring_start, (const void **)&v.ring_tw, (const void **)&v.tw,
         (const void **)&v.ring_rad, (const void **)&v.rad, (const void **)&v.ring_mx,
         (const void **)&v.ring_mfb, (const void **)&v.mfb, (const void **)&v.ring_mtw, (const void **)&v.mtw,
-        (const void **)&v.ring_M, (const void **)&v.ring_fb, (const void **)&v.fb, (const void **)&v.W,
         (const void **)&v.ring_ab, (const void **)&v.ab, (const void **)&v.ring_rdr, (const void **)&v.rdr,
         (const void **)&v.rdr_int, (const void **)&v.rdr_dbl,
         (const void **)&p->d_direct_rings, (const void **)&p->d_blue_rings, (const void **)&p->d_big_rings,
@@ -128,10 +127,10 @@ bool key_matches(const Header &h, const shtb_plan_s *p)
 bool write_payload(Writer &w, shtb_plan_s *p)
 {
     w.val(p->nrings); w.val(p->nhalf); w.val(p->npix); w.val(p->nalm); w.val(p->kind);
-    w.val(p->max_K_direct); w.val(p->max_M_mx); w.val(p->max_K_big); w.val(p->max_K_pow2); w.val(p->max_M_blue);
+    w.val(p->max_K_direct); w.val(p->max_M_mx); w.val(p->max_K_big);
     w.val(p->blue_split); w.val(p->max_M_small);
     w.val(p->chunk_kind); w.val(p->chunk_pix); w.val(p->stats);
-    w.vec(p->ring_J); w.vec(p->ring_s); w.vec(p->ring_M); w.vec(p->ring_start);
+    w.vec(p->ring_J); w.vec(p->ring_s); w.vec(p->ring_start);
     w.vec(p->direct_rings); w.vec(p->blue_rings); w.vec(p->big_rings);
     w.val(p->view);                                      // scalars; pointers are remapped below
     const int compressed = p->bf ? 1 : 0;
@@ -172,12 +171,12 @@ int read_payload(Reader &r, shtb_plan_s *p)
     int kind = -1;
     r.val(p->nrings); r.val(p->nhalf); r.val(p->npix); r.val(p->nalm); r.val(kind);
     if (r.ok && kind != p->kind) r.ok = false;
-    r.val(p->max_K_direct); r.val(p->max_M_mx); r.val(p->max_K_big); r.val(p->max_K_pow2); r.val(p->max_M_blue);
+    r.val(p->max_K_direct); r.val(p->max_M_mx); r.val(p->max_K_big);
     r.val(p->blue_split); r.val(p->max_M_small);
     r.val(p->chunk_kind); r.val(p->chunk_pix);
     shtb_plan_stats_t st{};          // set once the uploads (which count their bytes) are done
     r.val(st);
-    r.vec(p->ring_J, big); r.vec(p->ring_s, big); r.vec(p->ring_M, big); r.vec(p->ring_start, big);
+    r.vec(p->ring_J, big); r.vec(p->ring_s, big); r.vec(p->ring_start, big);
     r.vec(p->direct_rings, big); r.vec(p->blue_rings, big); r.vec(p->big_rings, big);
     if (r.ok && (p->blue_split < 0 || p->blue_split > (int)p->blue_rings.size())) r.ok = false;
     for (const auto &row : p->chunk_kind)

@@ -240,35 +240,6 @@ void sincospi_frac(long long num, long long den, double *c, double *s)
     *s = ss * sv;
 }
 
-bool is_pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
-
-long long next_pow2(long long x)
-{
-    long long p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
-// In-place radix-2 decimation-in-frequency FFT with exponent sign -1:
-// natural-order input, bit-reversed output.  The device kernels use the
-// same ordering, so filters built here can be multiplied pointwise there.
-void dif_forward(std::vector<std::complex<double>> &x, const std::vector<std::complex<double>> &W,
-                 long long Wlen)
-{
-    const long long M = (long long)x.size();
-    for (long long half = M / 2; half >= 1; half /= 2) {
-        const long long stride = Wlen / (2 * half);
-        for (long long blk = 0; blk < M; blk += 2 * half) {
-            for (long long j = 0; j < half; ++j) {
-                std::complex<double> u = x[blk + j], v = x[blk + j + half];
-                std::complex<double> w = std::conj(W[j * stride]);
-                x[blk + j] = u + v;
-                x[blk + j + half] = (u - v) * w;
-            }
-        }
-    }
-}
-
 // Radices of a mixed-radix transform of length n over 4, 2, 3, 5, 7, 11, 13
 // (4s first, at most one 2); false if n has another prime factor.
 bool radix_list(long long n, std::vector<int> &rl)
@@ -615,30 +586,7 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     p->stats.legendre_flops_per_map = 4.0 * (double)n_rec;
 
     // ------------------------------------------------------- ring FFT tables
-    // Per ring: K = J/2 (J is always even).  Radix-2 tables for the batch
-    // kernel: K a power of two -> in-place radix-2 FFT, otherwise Bluestein
-    // with M = next_pow2(2K - 1).
-    p->ring_M.assign(p->nrings, 0);
-    std::vector<long long> ring_tw(p->nrings), ring_fb(p->nrings, -1);
-    std::vector<int> pow2_blue;
-    p->max_K_pow2 = 0;
-    p->max_M_blue = 0;
-    long long Wlen = 2;
-    for (int r = 0; r < p->nrings; ++r) {
-        long long K = p->ring_J[r] / 2;
-        if (is_pow2(K)) {
-            p->max_K_pow2 = std::max<long long>(p->max_K_pow2, K);
-            Wlen = std::max(Wlen, K);
-        } else {
-            long long M = next_pow2(2 * K - 1);
-            p->ring_M[r] = (int)M;
-            pow2_blue.push_back(r);
-            p->max_M_blue = std::max<long long>(p->max_M_blue, M);
-            Wlen = std::max(Wlen, M);
-        }
-    }
-    if ((long long)std::max(p->max_K_pow2, p->max_M_blue) * 16 > 200 * 1024)
-        return shtb_fail(SHTB_ENOTSUP, "ring FFT does not fit in shared memory (nside too large)");
+    std::vector<long long> ring_tw(p->nrings);
 
     // e^{i pi n / J} tables, one per distinct J (north and south rings share)
     std::vector<double2> tw;
@@ -655,47 +603,6 @@ int shtb_build_dense_plan(shtb_plan_s *p)
         }
         ring_tw[r] = tw_of_J[J];
     }
-    // e^{2 pi i n / Wlen}
-    std::vector<double2> W(Wlen);
-    std::vector<std::complex<double>> Wc(Wlen);
-    for (long long n = 0; n < Wlen; ++n) {
-        double c, s;
-        sincospi_frac(2 * n, Wlen, &c, &s);
-        W[n] = make_double2(c, s);
-        Wc[n] = {c, s};
-    }
-    // Bluestein filters: for the positive-exponent DFT of length K,
-    //   X_n = c_n sum_k (Z_k c_k) conj(c_{n-k}),  c_j = e^{i pi j^2 / K},
-    // as a cyclic convolution of length M with b_j = conj(c_j) (|j| < K);
-    // stored as DIF_forward(b) / M in bit-reversed order.
-    std::vector<long long> fb_of_J(4 * N + 1, -1);
-    std::vector<int> distinct;
-    for (int r : pow2_blue)
-        if (fb_of_J[p->ring_J[r]] < 0) { fb_of_J[p->ring_J[r]] = 0; distinct.push_back(p->ring_J[r]); }
-    std::vector<long long> fb_off(distinct.size());
-    long long fb_total = 0;
-    for (size_t d = 0; d < distinct.size(); ++d) {
-        fb_off[d] = fb_total;
-        fb_of_J[distinct[d]] = fb_total;
-        fb_total += next_pow2(2 * (distinct[d] / 2) - 1);
-    }
-    std::vector<double2> fb((size_t)fb_total);
-    parallel_for((int)distinct.size(), nthreads, [&](int d) {
-        const long long K = distinct[d] / 2, M = next_pow2(2 * K - 1);
-        std::vector<std::complex<double>> bv(M, 0.0);
-        for (long long j = 0; j < K; ++j) {
-            double c, s;
-            sincospi_frac((j * j) % (2 * K), K, &c, &s);
-            std::complex<double> v(c, -s);
-            bv[j] = v;
-            if (j > 0) bv[M - j] = v;
-        }
-        dif_forward(bv, Wc, Wlen);
-        for (long long k = 0; k < M; ++k)
-            fb[fb_off[d] + k] = make_double2(bv[k].real() / M, bv[k].imag() / M);
-    });
-    for (int r : pow2_blue) ring_fb[r] = fb_of_J[p->ring_J[r]];
-
     // Mixed-radix tables of the stand-alone ring kernels: K factoring over
     // 2, 3, 5, 7, 11, 13 -> direct transform of length K; otherwise Bluestein
     // through the smallest 7-smooth length M >= 2K - 1.
@@ -942,7 +849,6 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     v.nhalf = Z;
     v.npix = p->npix;
     v.nalm = p->nalm;
-    v.Wlen = (int)Wlen;
     int rc;
 #define UP(field, vec)                                                                  \
     do {                                                                                \
@@ -968,10 +874,6 @@ int shtb_build_dense_plan(shtb_plan_s *p)
     UP(mfb, mfb);
     UP(ring_mtw, ring_mtw);
     UP(mtw, mtw);
-    UP(ring_M, p->ring_M);
-    UP(ring_fb, ring_fb);
-    UP(fb, fb);
-    UP(W, W);
     UP(ring_ab, ring_ab);
     UP(ab, ab);
     UP(ring_rdr, ring_rdr);
