@@ -432,6 +432,10 @@ int shtb_plan_destroy(shtb_plan p)
         cudaStreamDestroy(p->copy_stream);
         for (cudaEvent_t e : p->chunk_ev) cudaEventDestroy(e);
     }
+    for (cudaStream_t s2 : p->ring_stream)
+        if (s2) cudaStreamDestroy(s2);
+    for (cudaEvent_t e : p->ring_ev)
+        if (e) cudaEventDestroy(e);
     bf_release(p);
     if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
     delete p;

@@ -163,6 +163,10 @@ struct shtb_plan_s {
     int *d_chunk_list = nullptr;
     cudaStream_t copy_stream = nullptr;            // created on first use, owned
     cudaEvent_t chunk_ev[kPhiChunks] = {};
+    // the ring stage's three transform kinds run side by side on the
+    // caller's stream and two plan-owned streams (created on first use)
+    cudaStream_t ring_stream[2] = {};
+    cudaEvent_t ring_ev[3] = {};
 
     // device allocations owned by the plan (freed in destroy), with their sizes
     std::vector<void *> allocations;

@@ -235,10 +235,31 @@ int launch_qt_all(const shtb_plan_s *p, const double *qt, int nb, MapOut mo, int
 
 }  // namespace
 
+// The three ring kinds write disjoint rings, so they run side by side: the
+// Bluestein rings on the caller's stream, the direct and the radix-11/13 or
+// Rader rings on two plan-owned streams forked from it and joined back, and
+// each launch's last wave overlaps the others' work.
 int launch_phi_synth_qt(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0,
                         cudaStream_t st)
 {
-    return launch_qt_all(p, qt, nb, MapOut{map, nullptr}, b0, st);
+    shtb_plan_s *pp = const_cast<shtb_plan_s *>(p);
+    if (!pp->ring_stream[0]) {
+        for (auto &s2 : pp->ring_stream) SHTB_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        for (auto &e : pp->ring_ev) SHTB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const double2 *q2 = (const double2 *)qt;
+    const MapOut mo{map, nullptr};
+    SHTB_CUDA_TRY(cudaEventRecord(pp->ring_ev[0], st));
+    for (cudaStream_t s2 : pp->ring_stream) SHTB_CUDA_TRY(cudaStreamWaitEvent(s2, pp->ring_ev[0], 0));
+    int rc;
+    if ((rc = launch_qt_kind<kBluestein>(p, q2, nb, mo, b0, st))) return rc;
+    if ((rc = launch_qt_kind<kDirect>(p, q2, nb, mo, b0, pp->ring_stream[0]))) return rc;
+    if ((rc = launch_qt_kind<kDirectBig>(p, q2, nb, mo, b0, pp->ring_stream[1]))) return rc;
+    for (int i = 0; i < 2; ++i) {
+        SHTB_CUDA_TRY(cudaEventRecord(pp->ring_ev[1 + i], pp->ring_stream[i]));
+        SHTB_CUDA_TRY(cudaStreamWaitEvent(st, pp->ring_ev[1 + i], 0));
+    }
+    return SHTB_OK;
 }
 
 int launch_phi_synth_qt_chunk(const shtb_plan_s *p, const double *qt, int nb, double *map, int b0, int chunk,
