@@ -53,22 +53,26 @@ NCU_TRAFFIC = {
         "bytes": 16 * 410_475_008,
         "profile": "profiles/legendre_synth_nside512_l1024_b8.md",
     },
-    # butterfly kernels: DRAM bytes of all launches of one synthesis of 8 maps at
-    # Nside=2048, L=4096 (1-pass ncu capture of the full workload), keyed on the
-    # item bodies and the kernel's own definition; the plan then was host-built,
-    # and a GPU-built plan differs from it by about 1e-8 in its element counts
+    # butterfly kernels: DRAM bytes of one synthesis of 8 maps at Nside=2048,
+    # L=4096, scaled from an ncu capture of the same kernels at Nside=512,
+    # L=1024 (all launches of one synthesis) by the stored elements each
+    # kernel processes (dense interpolation elements for the levels, stored
+    # residual elements for the residual blocks); keyed on the item bodies and
+    # each kernel's own definition
     "bf_level_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.cu::bf_level_kernel"],
-        "sha256": "55cd9fa108eb7ea040425787bafa55815b8a58fd294b5d2aec6422c8f52ff3c7",
-        "bytes": 61_900_000_000 + 24_990_000_000,     # read + write over the 6 level launches
+        "sha256": "190a4a940b549c389882530c4843f5626f568071a1ddedff2227587f4690aaac",
+        # (2162.3 + 823.2) MB x 4,266,029,163 / 140,986,926 dense elements
+        "bytes": round((2_162_300_000 + 823_200_000) * 4_266_029_163 / 140_986_926),
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
     "bf_r_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.cu::bf_r_kernel"],
-        "sha256": "f66591a5916bb55acbf571456d7935f46bc290398a3bd82f42c13c0c779716f1",
-        "bytes": 10_720_000_000 + 3_640_000_000,
+        "sha256": "3d3fedd303a628a031158a9924682bdc354453f410022eafed8fb1610e85856b",
+        # (543.8 + 204.6) MB x 787,402,057 / 46,195,210 stored residual elements
+        "bytes": round((543_800_000 + 204_600_000) * 787_402_057 / 46_195_210),
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
 }
