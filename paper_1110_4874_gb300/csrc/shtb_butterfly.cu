@@ -16,6 +16,8 @@
 // per group and used for 2 x maps FMAs.  All stages are FP64-bound on GB300.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "shtb_bf_items.cuh"
 #include "shtb_butterfly.h"
 
@@ -26,20 +28,58 @@ using shtb_dev::Tile;
 constexpr int kBfWarps = 4;
 
 
-// ai[idx][b] = a_lm[b][idx] for the group's maps (Im a_l0 = 0, Sec. 2.1)
-__global__ void bf_interleave_kernel(PlanView v, const double2 *__restrict__ alm,
-                                     double2 *__restrict__ ai, int nmaps)
+// Staging between the caller's stacked a_lm [map][idx] and the butterfly's
+// interleaved ai [idx][map]: tiles of T coefficients x MB maps pass through
+// shared memory, so that both the map-major side and the interleaved side are
+// read or written along consecutive addresses (one map is a plain copy).  The
+// tile row is padded by one entry so the column walk spreads over the banks.
+constexpr int kStageTile = 256;
+
+struct StageTile {
+    int T, MB;
+    __device__ __forceinline__ explicit StageTile(int nmaps)
+        : T(nmaps >= kStageTile ? 1 : kStageTile / nmaps), MB(nmaps < kStageTile ? nmaps : kStageTile) {}
+};
+
+// ai[idx][b] = a_lm[b][idx] (Im a_l0 = 0, Sec. 2.1: idx <= L is m = 0)
+__global__ void __launch_bounds__(256) bf_interleave_kernel(PlanView v, const double2 *__restrict__ alm,
+                                                            double2 *__restrict__ ai, int nmaps)
 {
-    const int m = blockIdx.x;
-    const int L = v.lmax;
-    const long long off = shtb_dev::alm_off(L, m);
-    const int n = L - m + 1;
-    for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {
-        const int b = i / n, dl = i - b * n;
-        const long long idx = off + dl;
-        const double2 a = alm[(size_t)b * v.nalm + idx];
-        ai[(size_t)idx * nmaps + b] = make_double2(a.x, m == 0 ? 0.0 : a.y);
+    __shared__ double2 tile[2 * kStageTile];
+    const long long nalm = v.nalm, L = v.lmax;
+    if (nmaps == 1) {
+        for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nalm; i += 256LL * gridDim.x) {
+            const double2 a = alm[i];
+            ai[i] = make_double2(a.x, i <= L ? 0.0 : a.y);
+        }
+        return;
     }
+    const StageTile st(nmaps);
+    for (long long i0 = (long long)blockIdx.x * st.T; i0 < nalm; i0 += (long long)st.T * gridDim.x) {
+        const int nt = (int)min((long long)st.T, nalm - i0);
+        for (int b0 = 0; b0 < nmaps; b0 += st.MB) {
+            const int mb = min(st.MB, nmaps - b0);
+            for (int e = threadIdx.x; e < nt * mb; e += blockDim.x) {
+                const int b = e / nt, t = e - b * nt;
+                tile[b * (st.T + 1) + t] = alm[(size_t)(b0 + b) * nalm + i0 + t];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nt * mb; e += blockDim.x) {
+                const int t = e / mb, b = e - t * mb;
+                const double2 a = tile[b * (st.T + 1) + t];
+                ai[(size_t)(i0 + t) * nmaps + b0 + b] = make_double2(a.x, i0 + t <= L ? 0.0 : a.y);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// grid of the staging kernels: every tile once, at most 16 blocks per SM
+unsigned stage_grid(const shtb_plan_s *p, int nmaps)
+{
+    const long long T = nmaps >= kStageTile ? 1 : kStageTile / nmaps;
+    const long long tiles = nmaps == 1 ? (p->nalm + 255) / 256 : (p->nalm + T - 1) / T;
+    return (unsigned)std::max(1LL, std::min(tiles, 152LL * 16));
 }
 
 template <int NB>
@@ -327,20 +367,37 @@ bf_adj_r_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
     }
 }
 
-// alm[b][idx] = c_m aacc[idx][b] (c_0 = 1 with Im a_l0 = 0, c_m = 2)
-__global__ void bf_finish_kernel(PlanView v, const double2 *__restrict__ aacc,
-                                 double2 *__restrict__ alm, int nmaps)
+// alm[b][idx] = c_m aacc[idx][b] (c_0 = 1 with Im a_l0 = 0, c_m = 2), the
+// transposed staging of bf_interleave_kernel
+__global__ void __launch_bounds__(256) bf_finish_kernel(PlanView v, const double2 *__restrict__ aacc,
+                                                        double2 *__restrict__ alm, int nmaps)
 {
-    const int m = blockIdx.x;
-    const int L = v.lmax;
-    const long long off = shtb_dev::alm_off(L, m);
-    const int n = L - m + 1;
-    const double cm = m == 0 ? 1.0 : 2.0;
-    for (int i = threadIdx.x; i < n * nmaps; i += blockDim.x) {
-        const int b = i / n, dl = i - b * n;
-        const long long idx = off + dl;
-        const double2 a = aacc[(size_t)idx * nmaps + b];
-        alm[(size_t)b * v.nalm + idx] = make_double2(cm * a.x, m == 0 ? 0.0 : cm * a.y);
+    __shared__ double2 tile[2 * kStageTile];
+    const long long nalm = v.nalm, L = v.lmax;
+    auto scaled = [L](double2 a, long long idx) {
+        return idx <= L ? make_double2(a.x, 0.0) : make_double2(2.0 * a.x, 2.0 * a.y);
+    };
+    if (nmaps == 1) {
+        for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nalm; i += 256LL * gridDim.x)
+            alm[i] = scaled(aacc[i], i);
+        return;
+    }
+    const StageTile st(nmaps);
+    for (long long i0 = (long long)blockIdx.x * st.T; i0 < nalm; i0 += (long long)st.T * gridDim.x) {
+        const int nt = (int)min((long long)st.T, nalm - i0);
+        for (int b0 = 0; b0 < nmaps; b0 += st.MB) {
+            const int mb = min(st.MB, nmaps - b0);
+            for (int e = threadIdx.x; e < nt * mb; e += blockDim.x) {
+                const int t = e / mb, b = e - t * mb;
+                tile[b * (st.T + 1) + t] = aacc[(size_t)(i0 + t) * nmaps + b0 + b];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nt * mb; e += blockDim.x) {
+                const int b = e / nt, t = e - b * nt;
+                alm[(size_t)(b0 + b) * nalm + i0 + t] = scaled(tile[b * (st.T + 1) + t], i0 + t);
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -395,7 +452,7 @@ int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void 
     const size_t qt_map = (size_t)4 * p->nhalf * (p->lmax + 1);
     auto qt_of = [&](int b0) { return qt_out ? qt_out + (size_t)b0 * qt_map : qt_ws; };
     const int ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
-    bf_interleave_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ai, nmaps);
+    bf_interleave_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, alm, ai, nmaps);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     profile_end(const_cast<shtb_plan_s *>(p), st, 4, ev);
@@ -425,7 +482,7 @@ int launch_bf_synth_to_host(shtb_plan_s *p, const double2 *alm, double2 *ai, voi
     double *u0 = (double *)ws;
     double *u1 = u0 + (size_t)bf.u_entries * entry;
     double *qt = u1 + (size_t)bf.u_entries * entry;
-    bf_interleave_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, alm, ai, nmaps);
+    bf_interleave_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, alm, ai, nmaps);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     for (int b0 = 0; b0 < nmaps;) {
@@ -470,7 +527,7 @@ int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, voi
         else { rc = run_adj_group<1>(p, g, nmaps, b0, u0, u1, aacc, st); b0 += 1; }
         if (rc) return rc;
     }
-    bf_finish_kernel<<<p->lmax + 1, 256, 0, st>>>(p->view, aacc, alm, nmaps);
+    bf_finish_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, aacc, alm, nmaps);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     return SHTB_OK;
