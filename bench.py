@@ -318,7 +318,11 @@ def run_ours(args, rank, world, dist):
         for b in range(B):
             plan.synthesize(alm[b:b + 1], out=maps[b:b + 1])
     plain()
+    sh.shtb_profile_enable(plan.handle, True)
+    sh.shtb_profile_read(plan.handle)
     ms_plain = ms_per_map(timed(plain, args.steps), args.steps, B, world)
+    plain_stages, plain_calls = sh.shtb_profile_read(plan.handle)
+    sh.shtb_profile_enable(plan.handle, False)
 
     # ---- end to end through the C ABI with host buffers (copies inside)
     maps_h = torch.empty((B, plan.npix), dtype=torch.float64).pin_memory()
@@ -404,6 +408,8 @@ def run_ours(args, rank, world, dist):
         "details": {"adjoint_ms_per_map": round(ms_adj, 4), "plain_ms_per_map": round(ms_plain, 4),
                     "batched_over_plain": round(ms_plain / value, 3),
                     "stage_ms_per_step": {k: round(v / max(ncalls, 1), 3) for k, v in stages.items() if v},
+                    "plain_stage_ms_per_map": {k: round(v / max(plain_calls, 1), 3)
+                                               for k, v in plain_stages.items() if v},
                     "eps_plan": eps_plan, "compressed": bool(st["compressed"]),
                     "plan_build_s": round(plan_s, 2), "plan_built_on": built_on,
                     "plan_device_gb": round(st["plan_device_bytes"] / 1e9, 3),
@@ -423,10 +429,36 @@ def run_ours(args, rank, world, dist):
         plan_c4.close()
         out["details"]["polarised"] = polarised_synthesis(sh, synthetic, dev)
         out["details"]["plan_build"] = plan_build_compare(sh)
+        out["details"]["nside512_l1024"] = mid_size(sh, synthetic, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, cores, sample = oracle_sample(N, L, 1, args.cpu_rings, seed=2000)
         out["cpu_baseline"] = {"value": round(ms_cpu, 1), "unit": UNIT, "cores": cores,
                                "kind": "oracle", "sample": sample}
+    return out
+
+
+def mid_size(sh, synthetic, dev, N=512, L=1024, B=16, reps=5):
+    """Nside=512, L=1024 at eps = 1e-10 and 1e-12: 16 maps sharing one plan
+    in one call against the same maps one per call (ms/map each)."""
+    import torch
+    out = {}
+    for eps in (1e-10, 1e-12):
+        plan = sh.Plan(N, L, eps, leaf_cols=32, gpu_build=True)
+        plan.reserve(B)
+        alm = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=2000)).to(dev)
+        maps = torch.empty((B, plan.npix), dtype=torch.float64, device=dev)
+
+        def plain():
+            for b in range(B):
+                plan.synthesize(alm[b:b + 1], out=maps[b:b + 1])
+        ms_b = event_ms(lambda: plan.synthesize(alm, out=maps), reps) / B
+        ms_1 = event_ms(plain, reps) / B
+        out[f"eps{eps:g}"] = {"batched_ms_per_map": round(ms_b, 4), "plain_ms_per_map": round(ms_1, 4),
+                              "batched_over_plain": round(ms_1 / ms_b, 3), "maps": B,
+                              "n_dense": plan.stats()["n_dense"]}
+        plan.close()
+        del alm, maps
+        torch.cuda.empty_cache()
     return out
 
 

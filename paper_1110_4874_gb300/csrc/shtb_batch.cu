@@ -453,10 +453,12 @@ int build_schedule(shtb_batch_s *b, int warps, int width, int lpt)
     b->dev.next = b->dev.counters + ncounters;
     b->dev.err = b->dev.counters + ncounters + 1;
     b->dev.spin_limit = b->opts.spin_limit > 0 ? b->opts.spin_limit : 20000000LL;
-    // level-item scratch per warp: the batch's longest candidate list x
-    // (C + 1) doubles for its widest map group (C = 2 x maps)
+    // level-item scratch per warp: the batch's longest candidate list x the
+    // most doubles per candidate any of its map groups needs (C + 1 from 4
+    // maps up, 2 C below; C = 2 x maps)
     if (cmax > 16 || maxnc > shtb::kMaxCand) return shtb_fail(SHTB_EINVAL, "map group or candidate list too large");
-    b->dev.scratch = maxnc * (cmax + 1);
+    b->dev.scratch = maxnc * std::max(shtb_dev::level_scratch_per_cand(cmax),
+                                      shtb_dev::level_scratch_per_cand(std::min(cmax, 4)));
     b->ncounters = ncounters;
     b->stall_counter = 0;             // the first plan group's gather
     b->warps = warps;

@@ -103,15 +103,30 @@ __device__ __forceinline__ void bf_r_dispatch(int nr, const BfRItem &it, int L, 
     bf_r_pass<NB, NR, CG>(it, L, nhalf, ints, R, a0, astride, s0, sl, c, ubuf, qt);
 }
 
-// Few maps (C = 2 NB <= 4): a lane owns every component of its columns, so
-// one load of R[j][s] feeds C FMAs; the 32 lanes split the columns and each
-// column's sum runs over the rows in order, as with more maps (results do not
-// depend on how maps are grouped).  The row's C values of a are NB double2
-// loads shared by the warp.
-template <int NB, int NR, bool CG>
-__device__ __forceinline__ void bf_r_pass_cl(const BfRItem &it, int L, int nhalf, const int *__restrict__ ints,
-                                             const double *__restrict__ R, const double2 *a0, int astride,
-                                             int s0, int lane, double *ubuf, double *qt)
+// ---- few maps (C = 2 NB <= 4): packed dot products.  Every output of a
+// residual block (one column) and of a level child (one dense row) is a dot
+// product from zero over its inputs in order, whatever the map count, so the
+// results do not depend on how maps are grouped.  With C <= 4 components a
+// lane owns all components of its dot products (one load of the operator
+// feeds C FMAs), and the products of several blocks or children share the
+// warp: group g gets ceil(njobs_g / R) contiguous lanes, R the fewest rounds
+// that fit all groups on 32 lanes, and each lane runs its R products side by
+// side over the warp's longest input length (shorter groups idle there).
+
+// njobs dot products of length len: product x reads element i at
+// T[i * ld + x] and the NB complex inputs of entry i at v + i * vstep.
+struct DotGroup {
+    const double *T;
+    const double2 *v;
+    int len, njobs, ld, vstep;
+};
+
+// Sink: select(q) binds the lane's group (q a compile-time index after
+// unrolling), key(x) fetches what put needs to place product x, put(key, x,
+// acc) stores its C sums.
+template <int NB, int NR, bool CG, class Sink>
+__device__ __forceinline__ void packed_pass(const double *__restrict__ T, const double2 *v, int len, int ld,
+                                            int vstep, int kmax, int x0, int nl, int njobs, Sink &sink)
 {
     constexpr int C = 2 * NB;
     double acc[NR][C];
@@ -119,51 +134,174 @@ __device__ __forceinline__ void bf_r_pass_cl(const BfRItem &it, int L, int nhalf
     for (int r = 0; r < NR; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[r][c] = 0.0;
-    const int k = it.k;
-#pragma unroll 4
-    for (int j = 0; j < it.nrows; ++j) {
-        double2 a[NB];
+    bool ok[NR];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) a[b] = CG ? __ldcg(a0 + (size_t)j * astride + b) : __ldg(a0 + (size_t)j * astride + b);
-        const double *__restrict__ Rj = R + (size_t)j * k + s0 + lane;
+    for (int r = 0; r < NR; ++r) ok[r] = x0 + r * nl < njobs;
+    const double *__restrict__ Ti = T + x0;
+    const double2 *vi = v;
+#pragma unroll 2
+    for (int i = 0; i < kmax; ++i) {
+        const bool on = i < len;
+        double2 u[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            u[b] = make_double2(0.0, 0.0);
+            if (on) u[b] = CG ? __ldcg(vi + b) : __ldg(vi + b);
+        }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const double t = s0 + lane + 32 * r < k ? Rj[32 * r] : 0.0;
+            double t = 0.0;
+            if (on && ok[r]) t = __ldg(Ti + r * nl);
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                acc[r][2 * b] = fma(t, a[b].x, acc[r][2 * b]);
-                acc[r][2 * b + 1] = fma(t, a[b].y, acc[r][2 * b + 1]);
+                acc[r][2 * b] = fma(t, u[b].x, acc[r][2 * b]);
+                acc[r][2 * b + 1] = fma(t, u[b].y, acc[r][2 * b + 1]);
             }
         }
+        Ti += ld;
+        vi += vstep;
     }
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const int sidx = s0 + lane + 32 * r;
-        if (sidx >= k) continue;
-        if (it.to_rings) {
-            const long long e = ints[it.out_off + sidx];
-#pragma unroll
-            for (int c = 0; c < C; ++c) qt_store(qt, e, nhalf, L, c, acc[r][c]);
-        } else {
-            double *dst = ubuf + (size_t)(it.out_off + sidx) * C;
-#pragma unroll
-            for (int c = 0; c < C; ++c) dst[c] = acc[r][c];
+    for (int r = 0; r < NR; ++r)
+        if (ok[r]) {
+            const int x = x0 + r * nl;
+            sink.put(sink.key(x), x, acc[r]);
         }
-    }
 }
 
-template <int NB, int NR, bool CG>
-__device__ __forceinline__ void bf_r_dispatch_cl(int nr, const BfRItem &it, int L, int nhalf, const int *ints,
-                                                 const double *R, const double2 *a0, int astride, int s0,
-                                                 int lane, double *ubuf, double *qt)
+template <int NB, int NR, bool CG, class Sink>
+__device__ __forceinline__ void packed_pass_dispatch(int nr, const double *T, const double2 *v, int len, int ld,
+                                                     int vstep, int kmax, int x0, int nl, int njobs, Sink &sink)
 {
     if constexpr (NR > 1) {
         if (nr < NR) {
-            bf_r_dispatch_cl<NB, NR - 1, CG>(nr, it, L, nhalf, ints, R, a0, astride, s0, lane, ubuf, qt);
+            packed_pass_dispatch<NB, NR - 1, CG>(nr, T, v, len, ld, vstep, kmax, x0, nl, njobs, sink);
             return;
         }
     }
-    bf_r_pass_cl<NB, NR, CG>(it, L, nhalf, ints, R, a0, astride, s0, lane, ubuf, qt);
+    packed_pass<NB, NR, CG>(T, v, len, ld, vstep, kmax, x0, nl, njobs, sink);
+}
+
+template <int NB, int NG, bool CG, class Sink>
+__device__ __forceinline__ void packed_dots(const DotGroup (&g)[NG], int lane, Sink &sink)
+{
+    static_assert(NG <= 32, "one lane per group at least");
+    constexpr int NRMAX = NB == 1 ? 4 : 2;       // rounds per pass
+    int kmax = 0, jobs = 0;
+#pragma unroll
+    for (int q = 0; q < NG; ++q)
+        if (g[q].len > 0 && g[q].njobs > 0) {
+            kmax = max(kmax, g[q].len);
+            jobs += g[q].njobs;
+        }
+    if (kmax == 0) return;
+    int R = max(1, (jobs + 31) / 32);
+    for (;; ++R) {
+        int need = 0;
+#pragma unroll
+        for (int q = 0; q < NG; ++q)
+            if (g[q].len > 0 && g[q].njobs > 0) need += (g[q].njobs + R - 1) / R;
+        if (need <= 32) break;
+    }
+    int x0 = 0, nl = 1, njobs = 0, len = 0, ld = 0, vstep = 0;
+    const double *T = nullptr;
+    const double2 *v = nullptr;
+    int l0 = 0;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        const int n = g[q].len > 0 && g[q].njobs > 0 ? (g[q].njobs + R - 1) / R : 0;
+        if (lane >= l0 && lane < l0 + n) {
+            sink.select(q);
+            x0 = lane - l0;
+            nl = n;
+            njobs = g[q].njobs;
+            len = g[q].len;
+            ld = g[q].ld;
+            vstep = g[q].vstep;
+            T = g[q].T;
+            v = g[q].v;
+        }
+        l0 += n;
+    }
+    for (int r0 = 0; r0 < R; r0 += NRMAX)
+        packed_pass_dispatch<NB, NRMAX, CG>(min(NRMAX, R - r0), T, v, len, ld, vstep, kmax, x0 + r0 * nl, nl,
+                                            njobs, sink);
+}
+
+// residual blocks: column x of block q goes to its u entry, or to the q^t
+// entry the block lists (blocks at depth 0)
+template <int NB, int NG>
+struct RSink {
+    static constexpr int C = 2 * NB;
+    double *ubuf[NG];
+    const int *ent[NG];               // non-null: to_rings
+    long long out_off[NG];
+    int L, nhalf;
+    double *qt;
+    double *my_u;
+    const int *my_ent;
+    long long my_off;
+    __device__ __forceinline__ void select(int q)
+    {
+        my_u = ubuf[q];
+        my_ent = ent[q];
+        my_off = out_off[q];
+    }
+    __device__ __forceinline__ int key(int x) const { return my_ent ? __ldg(my_ent + x) : x; }
+    __device__ __forceinline__ void put(int key, int x, const double (&acc)[C]) const
+    {
+        if (my_ent) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) qt_store(qt, key, nhalf, L, c, acc[c]);
+        } else {
+            double *dst = my_u + (size_t)(my_off + x) * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) dst[c] = acc[c];
+        }
+    }
+};
+
+// Up to NG residual blocks (it[q] for q < n) on one warp at C = 2 NB <= 4:
+// u_s = sum_j R[j][s] a_j, column s of each block one dot product.  Block
+// q writes u1 if depth_par (non-null) marks its chain's depth odd, else u0.
+template <int NB, int NG, bool CG>
+__device__ __forceinline__ void bf_r_items_few(const BfRItem (&it)[NG], int n, int L, int nhalf,
+                                               const int *__restrict__ ints, const double *__restrict__ dbl,
+                                               const double2 *ai, int nmaps, int b0, double *u0, double *u1,
+                                               const int *__restrict__ depth_par, double *qt, int lane)
+{
+    DotGroup g[NG];
+    RSink<NB, NG> sink;
+    sink.L = L;
+    sink.nhalf = nhalf;
+    sink.qt = qt;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        const bool on = q < n;
+        const long long aoff = on ? alm_off(L, it[q].m) + it[q].t + 2 * it[q].j0 : 0;
+        g[q].T = dbl + (on ? it[q].data_off : 0);
+        g[q].v = ai + (size_t)aoff * nmaps + b0;
+        g[q].len = on ? it[q].nrows : 0;
+        g[q].njobs = on ? it[q].k : 0;
+        g[q].ld = on ? it[q].k : 0;
+        g[q].vstep = 2 * nmaps;
+        sink.ubuf[q] = on && depth_par && depth_par[it[q].m * 2 + it[q].t] ? u1 : u0;
+        sink.ent[q] = on && it[q].to_rings ? ints + it[q].out_off : nullptr;
+        sink.out_off[q] = on ? it[q].out_off : 0;
+    }
+    // a block without rows (a cropped chain range) still writes its columns:
+    // zero sums
+    constexpr int C = 2 * NB;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        if (q >= n || it[q].nrows > 0) continue;
+        for (int x = lane; x < it[q].k * C; x += 32) {
+            const int s = x / C, c = x - s * C;
+            if (sink.ent[q]) qt_store(qt, sink.ent[q][s], nhalf, L, c, 0.0);
+            else sink.ubuf[q][(size_t)(sink.out_off[q] + s) * C + c] = 0.0;
+        }
+    }
+    packed_dots<NB, NG, CG>(g, lane, sink);
 }
 
 // u = R^T a over one residual block.  ai: [idx][nmaps] complex, the group's
@@ -179,12 +317,8 @@ __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, int nhalf, c
     const double *__restrict__ R = dbl + it.data_off;
     const long long aoff = alm_off(L, it.m) + it.t;   // chain row j at aoff + 2j
     if constexpr (NB <= 2) {
-        constexpr int NRMAX = 4;
-        const double2 *a0 = ai + (size_t)(aoff + 2 * it.j0) * nmaps + b0;
-        for (int s0 = 0; s0 < it.k; s0 += 32 * NRMAX) {
-            const int nr = min(NRMAX, (it.k - s0 + 31) / 32);
-            bf_r_dispatch_cl<NB, NRMAX, CG>(nr, it, L, nhalf, ints, R, a0, 2 * nmaps, s0, lane, ubuf, qt);
-        }
+        const BfRItem one[1] = {it};
+        bf_r_items_few<NB, 1, CG>(one, 1, L, nhalf, ints, dbl, ai, nmaps, b0, ubuf, ubuf, nullptr, qt, lane);
         return;
     }
     const int sl = lane % LD, c = lane / LD;
@@ -198,8 +332,9 @@ __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, int nhalf, c
 
 // One level item: v = T_top^T u_top + T_bot^T u_bot over the shared
 // candidate list, written to the parent level's u (or to q^t at level 1).
-// out: this warp's shared-memory scratch of nc x (C + 1) doubles (the odd row
-// stride spreads the lanes' rows over the banks).
+// out: this warp's shared-memory scratch of nc x level_scratch_per_cand(C)
+// doubles (from 4 maps up, rows of C + 1: the odd stride spreads the lanes'
+// rows over the banks).
 template <int C>
 __host__ __device__ constexpr int out_stride()
 {
@@ -256,84 +391,106 @@ __device__ __forceinline__ void bf_dense_dispatch(int nr, int k, int nd, const d
     bf_dense_pass<NB, NR, CG>(k, nd, T, dpos, uc, q0, dl, c, out, second);
 }
 
-// Few maps (C = 2 NB <= 4): the two children run side by side, lanes 16 h
-// to 16 h + 15 on child h, each lane owning every component of its dense
-// rows d = dl + 16 r (r < NR; nd < 128 = 16 x 8, so one pass), so one load
-// of T[i][d] feeds C FMAs.  Each row's dot product runs over i in order from
-// zero, as in bf_dense_pass; the first child's rows and identity entries are
-// stored, then the second child's are added: the same arithmetic as with
-// more maps, bit for bit.
-template <int NB, int NR, bool CG>
-__device__ __forceinline__ void bf_pair_rows(const BfItem &it, const int *__restrict__ ints,
-                                             const double *__restrict__ dbl, const double *uin, double *out,
-                                             int lane)
+// Level-item scratch per candidate (doubles) and map group: C + 1 (one
+// padded row per candidate) from 4 maps up; with fewer maps each child sums
+// into its own zeroed nc x C half, so 2 C.
+__host__ __device__ constexpr int level_scratch_per_cand(int C)
 {
-    constexpr int C = 2 * NB, OS = out_stride<C>();
-    const int h = lane >> 4, dl = lane & 15;
-    const int k = it.k[h], nd = it.nd[h];
-    const int kmax = max(it.nd[0], it.nd[1]) ? max(it.k[0], it.k[1]) : 0;
-    const double2 *u2 = reinterpret_cast<const double2 *>(uin + (size_t)it.u_off[h] * C);
-    const double *__restrict__ Tq = dbl + it.T_off[h] + dl;
-    const int *__restrict__ dpos = ints + it.dpos_off[h];
-    double acc[NR][C];
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[r][c] = 0.0;
-#pragma unroll 2
-    for (int i = 0; i < kmax; ++i) {
-        if (i < k) {
-            double2 uv[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) uv[b] = CG ? __ldcg(u2 + (size_t)i * NB + b) : __ldg(u2 + (size_t)i * NB + b);
-            const double *__restrict__ Ti = Tq + (size_t)i * nd;
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const double t = dl + 16 * r < nd ? Ti[16 * r] : 0.0;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    acc[r][2 * b] = fma(t, uv[b].x, acc[r][2 * b]);
-                    acc[r][2 * b + 1] = fma(t, uv[b].y, acc[r][2 * b + 1]);
-                }
-            }
-        }
-    }
-    for (int s = 0; s < 2; ++s) {
-        if (h == s) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const int d = dl + 16 * r;
-                if (d < nd) {
-                    double *o = out + dpos[d] * OS;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) o[c] = s ? o[c] + acc[r][c] : acc[r][c];
-                }
-            }
-        }
-        // identity entries of child s: a store for the first child, an add
-        // for the second
-        const double *us = uin + (size_t)it.u_off[s] * C;
-        const int *__restrict__ ipos = ints + it.ipos_off[s];
-        for (int x = lane; x < it.k[s] * C; x += 32) {
-            const int i = x / C, cc = x - i * C;
-            double *o = out + ipos[i] * OS + cc;
-            *o = s ? *o + ldp<CG>(us + x) : ldp<CG>(us + x);
-        }
-        __syncwarp();
-    }
+    return C <= 4 ? 2 * C : C + 1;
 }
 
-template <int NB, int NR, bool CG>
-__device__ __forceinline__ void bf_pair_dispatch(int nr, const BfItem &it, const int *ints, const double *dbl,
-                                                 const double *uin, double *out, int lane)
+// level children: dense row x of child h lands on its candidate position in
+// that child's half of the item's scratch
+template <int NB, int NG>
+struct LSink {
+    static constexpr int C = 2 * NB;
+    double *S[NG];
+    const int *pos[NG];
+    double *my_S;
+    const int *my_pos;
+    __device__ __forceinline__ void select(int q)
+    {
+        my_S = S[q];
+        my_pos = pos[q];
+    }
+    __device__ __forceinline__ int key(int x) const { return __ldg(my_pos + x); }
+    __device__ __forceinline__ void put(int key, int, const double (&acc)[C]) const
+    {
+#pragma unroll
+        for (int c = 0; c < C; ++c) my_S[key * C + c] = acc[c];
+    }
+};
+
+// Up to G level items (it[q] for q < n) on one warp at C = 2 NB <= 4.  Each
+// child h sums into its own zeroed half S_h (identity entries copied, dense
+// rows as packed dot products); the output is S_0 + S_1, which is what the
+// wider groups' store-then-add order gives, bit for bit: 0 + v = v, and a
+// position with both children is c_0 + c_1 in both.  scr: G x 2 x maxnc x C
+// doubles of this warp's shared memory.
+template <int NB, int G, bool CG>
+__device__ __forceinline__ void bf_level_items_few(const BfItem (&it)[G], int n, int L, int nhalf,
+                                                   const int *__restrict__ ints, const double *__restrict__ dbl,
+                                                   const double *uin, double *uout, double *qt, double *scr,
+                                                   int maxnc, int lane)
 {
-    if constexpr (NR > 1) {
-        if (nr < NR) {
-            bf_pair_dispatch<NB, NR - 1, CG>(nr, it, ints, dbl, uin, out, lane);
-            return;
+    constexpr int C = 2 * NB;
+    DotGroup g[2 * G];
+    LSink<NB, 2 * G> sink;
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        const int nc = q < n ? it[q].nc : 0;
+        double *S0 = scr + (size_t)q * 2 * maxnc * C;
+        for (int i = lane; i < 2 * nc * C; i += 32) S0[i] = 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool on = q < n;
+            const double *u = uin + (on ? (size_t)it[q].u_off[h] * C : 0);
+            DotGroup &d = g[2 * q + h];
+            d.T = dbl + (on ? it[q].T_off[h] : 0);
+            d.v = reinterpret_cast<const double2 *>(u);
+            d.len = on ? it[q].k[h] : 0;
+            d.njobs = on ? it[q].nd[h] : 0;
+            d.ld = d.njobs;
+            d.vstep = NB;
+            sink.S[2 * q + h] = S0 + (size_t)h * nc * C;
+            sink.pos[2 * q + h] = ints + (on ? it[q].dpos_off[h] : 0);
         }
     }
-    bf_pair_rows<NB, NR, CG>(it, ints, dbl, uin, out, lane);
+    __syncwarp();
+    // identity entries (positions distinct from the same child's dense rows)
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        if (q >= n) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const double *u = uin + (size_t)it[q].u_off[h] * C;
+            const int *__restrict__ ipos = ints + it[q].ipos_off[h];
+            double *S = sink.S[2 * q + h];
+            for (int x = lane; x < it[q].k[h] * C; x += 32) {
+                const int i = x / C, cc = x - i * C;
+                S[ipos[i] * C + cc] = ldp<CG>(u + x);
+            }
+        }
+    }
+    packed_dots<NB, 2 * G, CG>(g, lane, sink);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        if (q >= n) break;
+        const int nc = it[q].nc;
+        const double *S0 = sink.S[2 * q], *S1 = S0 + (size_t)nc * C;
+        if (it[q].to_rings) {
+            const int *__restrict__ ent = ints + it[q].out_off;
+            for (int i = lane; i < nc * C; i += 32) {
+                const int cc = i / nc, cpos = i - cc * nc;
+                qt_store(qt, ent[cpos], nhalf, L, cc, S0[cpos * C + cc] + S1[cpos * C + cc]);
+            }
+        } else {
+            double *dst = uout + (size_t)it[q].out_off * C;
+            for (int i = lane; i < nc * C; i += 32) dst[i] = S0[i] + S1[i];
+        }
+    }
+    __syncwarp();
 }
 
 // Each child in turn: its dense rows (passes of up to LD x NRMAX rows, the
@@ -348,16 +505,16 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf
 {
     constexpr int C = 2 * NB, LD = Lanes<C>::LD, NRMAX = Lanes<C>::NRMAX;
     constexpr int OS = out_stride<C>();
+    if constexpr (NB <= 2) {
+        const BfItem one[1] = {it};
+        bf_level_items_few<NB, 1, CG>(one, 1, L, nhalf, ints, dbl, uin, uout, qt, out, it.nc, lane);
+        return;
+    }
     for (int i = lane; i < it.nc * OS; i += 32) out[i] = 0.0;
     __syncwarp();
     const int dl = lane % LD, c = lane / LD;
-    if constexpr (NB <= 2) {
-        const int nr = (max(it.nd[0], it.nd[1]) + 15) / 16;      // <= 8: nd < kMaxCand
-        bf_pair_dispatch<NB, 8, CG>(max(nr, 1), it, ints, dbl, uin, out, lane);
-    }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        if constexpr (NB <= 2) break;
         const int k = it.k[s], nd = it.nd[s];
         const double *u = uin + (size_t)it.u_off[s] * C;
         const double *__restrict__ T = dbl + it.T_off[s];

@@ -26,6 +26,29 @@ namespace {
 using shtb_dev::Tile;
 
 constexpr int kBfWarps = 4;
+// with one or two maps, a warp takes this many consecutive level items or
+// residual blocks (their dot products packed on its lanes)
+constexpr int kBfLevelPack = 2;
+constexpr int kBfResidualPack = 4;
+
+template <int NB>
+__host__ __device__ constexpr int items_per_warp_level()
+{
+    return NB <= 2 ? kBfLevelPack : 1;
+}
+
+template <int NB>
+__host__ __device__ constexpr int items_per_warp_residual()
+{
+    return NB <= 2 ? kBfResidualPack : 1;
+}
+
+// level-item scratch of one warp (doubles)
+template <int NB>
+__host__ __device__ constexpr size_t level_scratch_doubles(int maxnc)
+{
+    return (size_t)items_per_warp_level<NB>() * maxnc * shtb_dev::level_scratch_per_cand(2 * NB);
+}
 
 
 // Staging between the caller's stacked a_lm [map][idx] and the butterfly's
@@ -91,6 +114,18 @@ bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int
 {
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * kBfWarps + (threadIdx.x >> 5);
+    if constexpr (NB <= 2) {
+        constexpr int G = kBfResidualPack;
+        const int i0 = w * G;
+        if (i0 >= nitems) return;
+        const int n = min(G, nitems - i0);
+        BfRItem it[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) it[q] = items[i0 + min(q, n - 1)];
+        shtb_dev::bf_r_items_few<NB, G, false>(it, n, v.lmax, v.nhalf, ints, dbl, ai, nmaps, b0, ubuf0, ubuf1,
+                                               depth_par, qt, lane);
+        return;
+    }
     if (w >= nitems) return;
     const BfRItem it = items[w];
     double *ubuf = depth_par[it.m * 2 + it.t] ? ubuf1 : ubuf0;
@@ -98,19 +133,29 @@ bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int
 }
 
 template <int NB>
-__global__ void __launch_bounds__(32 * kBfWarps)
+__global__ void __launch_bounds__(32 * kBfWarps, NB <= 2 ? 6 : 8)
 bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, int maxnc,
                 const int *__restrict__ ints, const double *__restrict__ dbl,
                 const double *__restrict__ uin, double *__restrict__ uout, double *__restrict__ qt)
 {
-    constexpr int OS = shtb_dev::out_stride<2 * NB>();
-    extern __shared__ double sout[];     // [kBfWarps][maxnc * OS]
+    extern __shared__ double sout[];     // [kBfWarps][level_scratch_doubles<NB>(maxnc)]
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int w = blockIdx.x * kBfWarps + wib;
+    double *scr = sout + (size_t)wib * level_scratch_doubles<NB>(maxnc);
+    if constexpr (NB <= 2) {
+        constexpr int G = kBfLevelPack;
+        const int i0 = w * G;
+        if (i0 >= nitems) return;
+        const int n = min(G, nitems - i0);
+        BfItem it[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) it[q] = items[i0 + min(q, n - 1)];
+        shtb_dev::bf_level_items_few<NB, G, false>(it, n, L, nhalf, ints, dbl, uin, uout, qt, scr, maxnc, lane);
+        return;
+    }
     if (w >= nitems) return;
-    shtb_dev::bf_level_item<NB, false>(items[w], L, nhalf, ints, dbl, uin, uout, qt,
-                                       sout + (size_t)wib * maxnc * OS, lane);
+    shtb_dev::bf_level_item<NB, false>(items[w], L, nhalf, ints, dbl, uin, uout, qt, scr, lane);
 }
 
 // residual blocks of one map group (maps b0 .. b0+NB-1 of ai)
@@ -120,7 +165,8 @@ int launch_r(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double 
 {
     const BfPlanDev &bf = *p->bf;
     if (bf.n_ritems == 0) return SHTB_OK;
-    const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
+    const long long warps = (bf.n_ritems + items_per_warp_residual<NB>() - 1) / items_per_warp_residual<NB>();
+    const unsigned grid = (unsigned)((warps + kBfWarps - 1) / kBfWarps);
     bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(p->view, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
                                                     nmaps, b0, u0, u1, bf.depth_parity, qt);
     SHTB_CUDA_TRY(cudaGetLastError());
@@ -138,9 +184,10 @@ int launch_levels(const shtb_plan_s *p, double *u0, double *u1, double *qt, cuda
         if (n == 0) continue;
         double *uin = (lev % 2) ? u1 : u0;
         double *uout = ((lev - 1) % 2) ? u1 : u0;
-        const unsigned grid = (unsigned)((n + kBfWarps - 1) / kBfWarps);
+        const int warps = (n + items_per_warp_level<NB>() - 1) / items_per_warp_level<NB>();
+        const unsigned grid = (unsigned)((warps + kBfWarps - 1) / kBfWarps);
         const int maxnc = bf.level_maxnc[lev - 1];
-        const size_t smem = sizeof(double) * kBfWarps * maxnc * shtb_dev::out_stride<2 * NB>();
+        const size_t smem = sizeof(double) * kBfWarps * level_scratch_doubles<NB>(maxnc);
         SHTB_CUDA_TRY(cudaFuncSetAttribute(bf_level_kernel<NB>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         bf_level_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, p->lmax,
