@@ -103,15 +103,16 @@ __device__ __forceinline__ void bf_r_dispatch(int nr, const BfRItem &it, int L, 
     bf_r_pass<NB, NR, CG>(it, L, nhalf, ints, R, a0, astride, s0, sl, c, ubuf, qt);
 }
 
-// ---- few maps (C = 2 NB <= 4): packed dot products.  Every output of a
-// residual block (one column) and of a level child (one dense row) is a dot
-// product from zero over its inputs in order, whatever the map count, so the
-// results do not depend on how maps are grouped.  With C <= 4 components a
-// lane owns all components of its dot products (one load of the operator
-// feeds C FMAs), and the products of several blocks or children share the
-// warp: group g gets ceil(njobs_g / R) contiguous lanes, R the fewest rounds
-// that fit all groups on 32 lanes, and each lane runs its R products side by
-// side over the warp's longest input length (shorter groups idle there).
+// ---- level items with few maps (C = 2 NB <= 4): packed dot products.
+// Every output of a residual block (one column) and of a level child (one
+// dense row) is a dot product from zero over its inputs in order, whatever
+// the map count, so the results do not depend on how maps are grouped.  With
+// C <= 4 components a lane owns all components of its dot products (one load
+// of the operator feeds C FMAs), and the products of several children share
+// the warp: group g gets ceil(njobs_g / R) contiguous lanes, R the fewest
+// rounds that fit all groups on 32 lanes, and each lane runs its R products
+// side by side over the warp's longest input length (shorter groups idle
+// there).  Up to 4 (8) products per lane share each input load.
 
 // njobs dot products of length len: product x reads element i at
 // T[i * ld + x] and the NB complex inputs of entry i at v + i * vstep.
@@ -228,80 +229,189 @@ __device__ __forceinline__ void packed_dots(const DotGroup (&g)[NG], int lane, S
                                             njobs, sink);
 }
 
-// residual blocks: column x of block q goes to its u entry, or to the q^t
-// entry the block lists (blocks at depth 0)
-template <int NB, int NG>
-struct RSink {
-    static constexpr int C = 2 * NB;
-    double *ubuf[NG];
-    const int *ent[NG];               // non-null: to_rings
-    long long out_off[NG];
-    int L, nhalf;
-    double *qt;
-    double *my_u;
-    const int *my_ent;
-    long long my_off;
-    __device__ __forceinline__ void select(int q)
-    {
-        my_u = ubuf[q];
-        my_ent = ent[q];
-        my_off = out_off[q];
-    }
-    __device__ __forceinline__ int key(int x) const { return my_ent ? __ldg(my_ent + x) : x; }
-    __device__ __forceinline__ void put(int key, int x, const double (&acc)[C]) const
-    {
-        if (my_ent) {
-#pragma unroll
-            for (int c = 0; c < C; ++c) qt_store(qt, key, nhalf, L, c, acc[c]);
-        } else {
-            double *dst = my_u + (size_t)(my_off + x) * C;
-#pragma unroll
-            for (int c = 0; c < C; ++c) dst[c] = acc[c];
-        }
-    }
+// ---- residual blocks with few maps: dot products packed in rounds.  One
+// warp takes the columns of several blocks (each column, per real component,
+// a dot product from zero over the block's rows in order, as above): a lane
+// owns CPL components of one column (S = C / CPL lanes per column), the
+// warp's columns are ordered by length, longest first, and cut into rounds of
+// 32 lanes; a round runs over its longest column, so columns of similar
+// length share a round and few FMA slots idle.  (Tried on the level items
+// too, where every lane loading its own input for one product measured
+// slower than the packing above.)
+
+// Group descriptor, held by lane q for group q: rows dot products of length
+// len, row x reading element i at T[i * ld + x] and the components of input
+// entry i at v + i * vstep (doubles); row x lands on output slot pos[x] (x
+// when pos is null), slot s at base[s * C + c], or at q^t entry ent[s] when
+// base is null.
+struct RoundGroup {
+    const double *T;
+    const double *v;
+    const int *pos;
+    double *base;
+    const int *ent;
+    int len, rows, ld, vstep;
 };
 
-// Up to NG residual blocks (it[q] for q < n) on one warp at C = 2 NB <= 4:
-// u_s = sum_j R[j][s] a_j, column s of each block one dot product.  Block
-// q writes u1 if depth_par (non-null) marks its chain's depth odd, else u0.
-template <int NB, int NG, bool CG>
-__device__ __forceinline__ void bf_r_items_few(const BfRItem (&it)[NG], int n, int L, int nhalf,
+template <class P>
+__device__ __forceinline__ P shfl_ptr(P p, int src)
+{
+    return (P)__shfl_sync(0xffffffffu, (unsigned long long)p, src);
+}
+
+// address of component c of q^t entry e (see qt_store)
+__device__ __forceinline__ double *qt_ptr(double *qt, long long e, int nhalf, int L, int c)
+{
+    const long long mt = e / nhalf, r = e - mt * nhalf;
+    const long long m = mt >> 1, t = mt & 1;
+    const int b = c >> 1;
+    return qt + ((((long long)b * 2 + t) * nhalf + r) * (L + 1) + m) * 2 + (c & 1);
+}
+
+template <int C>
+__device__ __forceinline__ double *slot_ptr(double *base, const int *ent, int slot, int c, double *qt, int nhalf,
+                                            int L)
+{
+    return base ? base + (size_t)slot * C + c : qt_ptr(qt, __ldg(ent + slot), nhalf, L, c);
+}
+
+// The rows of the NG groups (lane q < NG holds group q in g) on one warp;
+// ADD: outputs are added to what is there, else stored.
+template <int NB, int CPL, int NG, bool CG, bool ADD>
+__device__ __forceinline__ void round_dots(const RoundGroup &g, int L, int nhalf, double *qt,
+                                           const double *safe, int lane)
+{
+    constexpr int C = 2 * NB, S = C / CPL;
+    static_assert(NG <= 32 && S * CPL == C, "lane layout");
+    // every lane: each group's length and lane count, then the groups ordered
+    // by length (longest first, ties by index) and their first lanes
+    int len[NG], jobs[NG];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        len[q] = __shfl_sync(0xffffffffu, lane < NG ? g.len : 0, q);
+        const int rows = __shfl_sync(0xffffffffu, lane < NG ? g.rows : 0, q);
+        jobs[q] = len[q] > 0 ? S * rows : 0;
+        if (jobs[q] == 0) len[q] = 0;
+    }
+    int start[NG], total = 0;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        int st = 0;
+#pragma unroll
+        for (int p = 0; p < NG; ++p)
+            if (len[p] > len[q] || (len[p] == len[q] && p < q)) st += jobs[p];
+        start[q] = st;
+        total += jobs[q];
+    }
+    for (int r0 = 0; r0 < total; r0 += 32) {
+        const int rho = r0 + lane;
+        int q = -1;
+#pragma unroll
+        for (int p = 0; p < NG; ++p)
+            if (rho >= start[p] && rho < start[p] + jobs[p]) q = p;
+        const int src = q < 0 ? 0 : q;
+        const double *__restrict__ T = shfl_ptr(g.T, src);
+        const double *v = shfl_ptr(g.v, src);
+        const int ld = __shfl_sync(0xffffffffu, g.ld, src);
+        const int vstep = __shfl_sync(0xffffffffu, g.vstep, src);
+        const int *pos = shfl_ptr(g.pos, src);
+        double *base = shfl_ptr(g.base, src);
+        const int *ent = shfl_ptr(g.ent, src);
+        int mylen = 0, x = 0, c0 = 0;
+#pragma unroll
+        for (int p = 0; p < NG; ++p)
+            if (p == q) {
+                mylen = len[p];
+                x = (rho - start[p]) / S;
+                c0 = (rho - start[p] - x * S) * CPL;
+            }
+        const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)mylen);
+        const int slot = q >= 0 && pos ? __ldg(pos + x) : x;      // issued before the sums
+        double acc[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) acc[c] = 0.0;
+        const double *__restrict__ Ti = T + x;
+        const double *vi = v + c0;
+        // blocks of U inputs: all U loads issued before their FMAs (past its
+        // own length a lane reads a fixed valid, 16-byte aligned address and
+        // adds zero products); FMAs past the round's longest input are skipped
+        constexpr int U = 8;
+        for (int i0 = 0; i0 < kmax; i0 += U) {
+            double t[U], u[U][CPL];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const bool on = i0 + j < mylen;
+                const double tl = __ldg(on ? Ti : safe);
+                if constexpr (CPL == 1) {
+                    const double w = CG ? __ldcg(on ? vi : safe) : __ldg(on ? vi : safe);
+                    u[j][0] = on ? w : 0.0;
+                } else {
+                    const double2 *w2 = reinterpret_cast<const double2 *>(on ? vi : safe);
+                    const double2 w = CG ? __ldcg(w2) : __ldg(w2);
+                    u[j][0] = on ? w.x : 0.0;
+                    u[j][1] = on ? w.y : 0.0;
+                }
+                t[j] = on ? tl : 0.0;
+                Ti += ld;
+                vi += vstep;
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (i0 + j >= kmax) break;
+#pragma unroll
+                for (int c = 0; c < CPL; ++c) acc[c] = fma(t[j], u[j][c], acc[c]);
+            }
+        }
+        if (q >= 0) {
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                double *o = slot_ptr<C>(base, ent, slot, c0 + c, qt, nhalf, L);
+                *o = ADD ? *o + acc[c] : acc[c];
+            }
+        }
+    }
+}
+
+// Up to G residual blocks on one warp at C = 2 NB <= 4 (items[q] for
+// q < n): u_s = sum_j R[j][s] a_j, column s of each block one dot product.
+// Block q writes u1 if depth_par (non-null) marks its chain's depth odd,
+// else u0.
+template <int NB, int G, bool CG>
+__device__ __forceinline__ void bf_r_items_few(const BfRItem *__restrict__ items, int n, int L, int nhalf,
                                                const int *__restrict__ ints, const double *__restrict__ dbl,
                                                const double2 *ai, int nmaps, int b0, double *u0, double *u1,
                                                const int *__restrict__ depth_par, double *qt, int lane)
 {
-    DotGroup g[NG];
-    RSink<NB, NG> sink;
-    sink.L = L;
-    sink.nhalf = nhalf;
-    sink.qt = qt;
-#pragma unroll
-    for (int q = 0; q < NG; ++q) {
-        const bool on = q < n;
-        const long long aoff = on ? alm_off(L, it[q].m) + it[q].t + 2 * it[q].j0 : 0;
-        g[q].T = dbl + (on ? it[q].data_off : 0);
-        g[q].v = ai + (size_t)aoff * nmaps + b0;
-        g[q].len = on ? it[q].nrows : 0;
-        g[q].njobs = on ? it[q].k : 0;
-        g[q].ld = on ? it[q].k : 0;
-        g[q].vstep = 2 * nmaps;
-        sink.ubuf[q] = on && depth_par && depth_par[it[q].m * 2 + it[q].t] ? u1 : u0;
-        sink.ent[q] = on && it[q].to_rings ? ints + it[q].out_off : nullptr;
-        sink.out_off[q] = on ? it[q].out_off : 0;
+    constexpr int C = 2 * NB;
+    // one component per lane at one map, one map's pair at two
+    constexpr int CPL = NB == 1 ? 1 : 2;
+    RoundGroup g{};
+    if (lane < n) {
+        const BfRItem it = items[lane];
+        const long long aoff = alm_off(L, it.m) + it.t + 2 * it.j0;
+        double *ubuf = depth_par && depth_par[it.m * 2 + it.t] ? u1 : u0;
+        g.T = dbl + it.data_off;
+        g.v = reinterpret_cast<const double *>(ai + (size_t)aoff * nmaps + b0);
+        g.pos = nullptr;
+        g.base = it.to_rings ? nullptr : ubuf + (size_t)it.out_off * C;
+        g.ent = it.to_rings ? ints + it.out_off : nullptr;
+        g.len = it.nrows;
+        g.rows = it.k;
+        g.ld = it.k;
+        g.vstep = 4 * nmaps;
     }
     // a block without rows (a cropped chain range) still writes its columns:
     // zero sums
-    constexpr int C = 2 * NB;
 #pragma unroll
-    for (int q = 0; q < NG; ++q) {
-        if (q >= n || it[q].nrows > 0) continue;
-        for (int x = lane; x < it[q].k * C; x += 32) {
-            const int s = x / C, c = x - s * C;
-            if (sink.ent[q]) qt_store(qt, sink.ent[q][s], nhalf, L, c, 0.0);
-            else sink.ubuf[q][(size_t)(sink.out_off[q] + s) * C + c] = 0.0;
-        }
+    for (int q = 0; q < G; ++q) {
+        const int len = __shfl_sync(0xffffffffu, g.len, q), rows = __shfl_sync(0xffffffffu, g.rows, q);
+        double *base = shfl_ptr(g.base, q);
+        const int *ent = shfl_ptr(g.ent, q);
+        if (q >= n || len > 0) continue;
+        for (int x = lane; x < rows * C; x += 32)
+            *slot_ptr<C>(base, ent, x / C, x % C, qt, nhalf, L) = 0.0;
     }
-    packed_dots<NB, NG, CG>(g, lane, sink);
+    round_dots<NB, CPL, G, CG, false>(g, L, nhalf, qt, dbl, lane);
 }
 
 // u = R^T a over one residual block.  ai: [idx][nmaps] complex, the group's
@@ -317,8 +427,7 @@ __device__ __forceinline__ void bf_r_item(const BfRItem &it, int L, int nhalf, c
     const double *__restrict__ R = dbl + it.data_off;
     const long long aoff = alm_off(L, it.m) + it.t;   // chain row j at aoff + 2j
     if constexpr (NB <= 2) {
-        const BfRItem one[1] = {it};
-        bf_r_items_few<NB, 1, CG>(one, 1, L, nhalf, ints, dbl, ai, nmaps, b0, ubuf, ubuf, nullptr, qt, lane);
+        bf_r_items_few<NB, 1, CG>(&it, 1, L, nhalf, ints, dbl, ai, nmaps, b0, ubuf, ubuf, nullptr, qt, lane);
         return;
     }
     const int sl = lane % LD, c = lane / LD;
@@ -499,17 +608,12 @@ __device__ __forceinline__ void bf_level_items_few(const BfItem (&it)[G], int n,
 // entry within a child; the warp syncs between the children, whose positions
 // may coincide.
 template <int NB, bool CG>
-__device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
-                                              const double *__restrict__ dbl, const double *uin,
-                                              double *uout, double *qt, double *out, int lane)
+__device__ __forceinline__ void bf_level_item_wide(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
+                                                   const double *__restrict__ dbl, const double *uin,
+                                                   double *uout, double *qt, double *out, int lane)
 {
     constexpr int C = 2 * NB, LD = Lanes<C>::LD, NRMAX = Lanes<C>::NRMAX;
     constexpr int OS = out_stride<C>();
-    if constexpr (NB <= 2) {
-        const BfItem one[1] = {it};
-        bf_level_items_few<NB, 1, CG>(one, 1, L, nhalf, ints, dbl, uin, uout, qt, out, it.nc, lane);
-        return;
-    }
     for (int i = lane; i < it.nc * OS; i += 32) out[i] = 0.0;
     __syncwarp();
     const int dl = lane % LD, c = lane / LD;
@@ -547,6 +651,19 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf
         }
     }
     __syncwarp();
+}
+
+template <int NB, bool CG>
+__device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
+                                              const double *__restrict__ dbl, const double *uin,
+                                              double *uout, double *qt, double *out, int lane)
+{
+    if constexpr (NB <= 2) {
+        const BfItem one[1] = {it};
+        bf_level_items_few<NB, 1, CG>(one, 1, L, nhalf, ints, dbl, uin, uout, qt, out, it.nc, lane);
+    } else {
+        bf_level_item_wide<NB, CG>(it, L, nhalf, ints, dbl, uin, uout, qt, out, lane);
+    }
 }
 
 }  // namespace shtb_dev

@@ -29,7 +29,7 @@ constexpr int kBfWarps = 4;
 // with one or two maps, a warp takes this many consecutive level items or
 // residual blocks (their dot products packed on its lanes)
 constexpr int kBfLevelPack = 2;
-constexpr int kBfResidualPack = 4;
+constexpr int kBfResidualPack = 8;
 
 template <int NB>
 __host__ __device__ constexpr int items_per_warp_level()
@@ -118,12 +118,8 @@ bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int
         constexpr int G = kBfResidualPack;
         const int i0 = w * G;
         if (i0 >= nitems) return;
-        const int n = min(G, nitems - i0);
-        BfRItem it[G];
-#pragma unroll
-        for (int q = 0; q < G; ++q) it[q] = items[i0 + min(q, n - 1)];
-        shtb_dev::bf_r_items_few<NB, G, false>(it, n, v.lmax, v.nhalf, ints, dbl, ai, nmaps, b0, ubuf0, ubuf1,
-                                               depth_par, qt, lane);
+        shtb_dev::bf_r_items_few<NB, G, false>(items + i0, min(G, nitems - i0), v.lmax, v.nhalf, ints, dbl, ai,
+                                               nmaps, b0, ubuf0, ubuf1, depth_par, qt, lane);
         return;
     }
     if (w >= nitems) return;
