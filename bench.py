@@ -62,17 +62,17 @@ NCU_TRAFFIC = {
     "bf_level_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.cu::bf_level_kernel"],
-        "sha256": "35ac2bac8bfc92b386b6c0e42b44ae2f7951561364de4ec88d26bd56873fda3d",
-        # (2152.1 + 812.4) MB x 4,266,029,163 / 140,986,926 dense elements
-        "bytes": round((2_152_100_000 + 812_400_000) * 4_266_029_163 / 140_986_926),
+        "sha256": "06b9e7a09d16be7486aa7ceb73c12caeb7b8b8df50f1ac49a2d63b093e7f3852",
+        # (2153.0 + 811.7) MB x 4,266,029,163 / 140,986,926 dense elements
+        "bytes": round((2_153_000_000 + 811_700_000) * 4_266_029_163 / 140_986_926),
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
     "bf_r_kernel": {
         "sources": ["paper_1110_4874_gb300/csrc/shtb_bf_items.cuh",
                     "paper_1110_4874_gb300/csrc/shtb_butterfly.cu::bf_r_kernel"],
-        "sha256": "739adec52898218ffe86f95aa460cb8727676e427c7ab631162f8fdb4970591d",
-        # (447.4 + 193.0) MB x 787,402,057 / 46,195,210 stored residual elements
-        "bytes": round((447_400_000 + 193_000_000) * 787_402_057 / 46_195_210),
+        "sha256": "a7f9b65a4a54b5fe181a4a547c65b3fad4279508730af57d9a3c50c700017a62",
+        # (447.3 + 193.9) MB x 787,402,057 / 46,195,210 stored residual elements
+        "bytes": round((447_300_000 + 193_900_000) * 787_402_057 / 46_195_210),
         "profile": "profiles/bf_level_kernel_nside2048_l4096_b8.md",
     },
 }

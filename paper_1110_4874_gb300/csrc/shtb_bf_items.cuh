@@ -39,12 +39,19 @@ __device__ __forceinline__ long long alm_off(int L, int m)
 // qt[((b * 2 + t) * nhalf + r) * (L + 1) + m], so the ring stage reads each
 // map's q_m of one ring contiguously in m.  Leaf outputs are addressed by the
 // entry e = (m * 2 + t) * nhalf + r; this writes the C = 2 NB components of e.
-__device__ __forceinline__ void qt_store(double *qt, long long e, int nhalf, int L, int c, double v)
+// Entries fit 32 bits (e < 2 (L + 1) nhalf), so the split of e runs as a
+// 32-bit division.
+__device__ __forceinline__ size_t qt_index(int e, int nhalf, int L, int c)
 {
-    const long long mt = e / nhalf, r = e - mt * nhalf;
-    const long long m = mt >> 1, t = mt & 1;
-    const int b = c >> 1;
-    qt[((((long long)b * 2 + t) * nhalf + r) * (L + 1) + m) * 2 + (c & 1)] = v;
+    const unsigned mt = (unsigned)e / (unsigned)nhalf, r = (unsigned)e - mt * (unsigned)nhalf;
+    const unsigned m = mt >> 1, t = mt & 1;
+    const unsigned b = (unsigned)c >> 1;
+    return ((((size_t)b * 2 + t) * nhalf + r) * (L + 1) + m) * 2 + (c & 1);
+}
+
+__device__ __forceinline__ void qt_store(double *qt, int e, int nhalf, int L, int c, double v)
+{
+    qt[qt_index(e, nhalf, L, c)] = v;
 }
 
 // Warp layout of the synthesis items: each lane owns ONE real component c of
@@ -260,12 +267,9 @@ __device__ __forceinline__ P shfl_ptr(P p, int src)
 }
 
 // address of component c of q^t entry e (see qt_store)
-__device__ __forceinline__ double *qt_ptr(double *qt, long long e, int nhalf, int L, int c)
+__device__ __forceinline__ double *qt_ptr(double *qt, int e, int nhalf, int L, int c)
 {
-    const long long mt = e / nhalf, r = e - mt * nhalf;
-    const long long m = mt >> 1, t = mt & 1;
-    const int b = c >> 1;
-    return qt + ((((long long)b * 2 + t) * nhalf + r) * (L + 1) + m) * 2 + (c & 1);
+    return qt + qt_index(e, nhalf, L, c);
 }
 
 template <int C>
@@ -591,8 +595,8 @@ __device__ __forceinline__ void bf_level_items_few(const BfItem (&it)[G], int n,
         if (it[q].to_rings) {
             const int *__restrict__ ent = ints + it[q].out_off;
             for (int i = lane; i < nc * C; i += 32) {
-                const int cc = i / nc, cpos = i - cc * nc;
-                qt_store(qt, ent[cpos], nhalf, L, cc, S0[cpos * C + cc] + S1[cpos * C + cc]);
+                const int cpos = i / C, cc = i - cpos * C;
+                qt_store(qt, ent[cpos], nhalf, L, cc, S0[i] + S1[i]);
             }
         } else {
             double *dst = uout + (size_t)it[q].out_off * C;
@@ -607,7 +611,9 @@ __device__ __forceinline__ void bf_level_items_few(const BfItem (&it)[G], int n,
 // identity positions are distinct, so lanes never update the same scratch
 // entry within a child; the warp syncs between the children, whose positions
 // may coincide.
-template <int NB, bool CG>
+// RING: 1 when every item of the launch writes q^t (the plan's level 1), 0
+// when none does, -1 to follow each item's to_rings flag.
+template <int NB, bool CG, int RING = -1>
 __device__ __forceinline__ void bf_level_item_wide(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
                                                    const double *__restrict__ dbl, const double *uin,
                                                    double *uout, double *qt, double *out, int lane)
@@ -637,10 +643,10 @@ __device__ __forceinline__ void bf_level_item_wide(const BfItem &it, int L, int 
         }
         __syncwarp();
     }
-    if (it.to_rings) {
+    if (RING == 1 || (RING < 0 && it.to_rings)) {
         const int *__restrict__ ent = ints + it.out_off;
         for (int i = lane; i < it.nc * C; i += 32) {
-            const int cc = i / it.nc, cpos = i - cc * it.nc;
+            const int cpos = i / C, cc = i - cpos * C;
             qt_store(qt, ent[cpos], nhalf, L, cc, out[cpos * OS + cc]);
         }
     } else {
@@ -653,7 +659,7 @@ __device__ __forceinline__ void bf_level_item_wide(const BfItem &it, int L, int 
     __syncwarp();
 }
 
-template <int NB, bool CG>
+template <int NB, bool CG, int RING = -1>
 __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf, const int *__restrict__ ints,
                                               const double *__restrict__ dbl, const double *uin,
                                               double *uout, double *qt, double *out, int lane)
@@ -662,7 +668,7 @@ __device__ __forceinline__ void bf_level_item(const BfItem &it, int L, int nhalf
         const BfItem one[1] = {it};
         bf_level_items_few<NB, 1, CG>(one, 1, L, nhalf, ints, dbl, uin, uout, qt, out, it.nc, lane);
     } else {
-        bf_level_item_wide<NB, CG>(it, L, nhalf, ints, dbl, uin, uout, qt, out, lane);
+        bf_level_item_wide<NB, CG, RING>(it, L, nhalf, ints, dbl, uin, uout, qt, out, lane);
     }
 }
 

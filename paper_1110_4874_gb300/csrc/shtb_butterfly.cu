@@ -128,7 +128,9 @@ bf_r_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const int
     shtb_dev::bf_r_item<NB, false>(it, v.lmax, v.nhalf, ints, dbl, ai, nmaps, b0, ubuf, qt, lane);
 }
 
-template <int NB>
+// RING: the launch is the plan's level 1, whose items all write q^t (no
+// other level's do), so each instantiation holds one output path.
+template <int NB, bool RING>
 __global__ void __launch_bounds__(32 * kBfWarps, NB <= 2 ? 6 : 8)
 bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, int maxnc,
                 const int *__restrict__ ints, const double *__restrict__ dbl,
@@ -151,7 +153,7 @@ bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, 
         return;
     }
     if (w >= nitems) return;
-    shtb_dev::bf_level_item<NB, false>(items[w], L, nhalf, ints, dbl, uin, uout, qt, scr, lane);
+    shtb_dev::bf_level_item<NB, false, RING ? 1 : 0>(items[w], L, nhalf, ints, dbl, uin, uout, qt, scr, lane);
 }
 
 // residual blocks of one map group (maps b0 .. b0+NB-1 of ai)
@@ -184,11 +186,10 @@ int launch_levels(const shtb_plan_s *p, double *u0, double *u1, double *qt, cuda
         const unsigned grid = (unsigned)((warps + kBfWarps - 1) / kBfWarps);
         const int maxnc = bf.level_maxnc[lev - 1];
         const size_t smem = sizeof(double) * kBfWarps * level_scratch_doubles<NB>(maxnc);
-        SHTB_CUDA_TRY(cudaFuncSetAttribute(bf_level_kernel<NB>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        bf_level_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, p->lmax,
-                                                               p->nhalf, maxnc, bf.ints, bf.dbl, uin,
-                                                               uout, qt);
+        auto *kern = lev == 1 ? bf_level_kernel<NB, true> : bf_level_kernel<NB, false>;
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, 32 * kBfWarps, smem, st>>>(bf.level_items[lev - 1], n, p->lmax, p->nhalf, maxnc, bf.ints,
+                                                bf.dbl, uin, uout, qt);
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
