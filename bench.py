@@ -426,6 +426,7 @@ def run_ours(args, rank, world, dist):
     if rank == 0 and not args.no_patterns:
         out["details"]["batched_serving"], plan_c4 = batched_serving(sh, synthetic, dev)
         out["details"]["differentiation"] = differentiation(sh, synthetic, dev, plan_c4)
+        out["details"]["regenerated_residual"] = regenerated_residual(sh, synthetic, dev, plan_c4)
         plan_c4.close()
         out["details"]["polarised"] = polarised_synthesis(sh, synthetic, dev)
         out["details"]["plan_build"] = plan_build_compare(sh)
@@ -572,6 +573,29 @@ def differentiation(sh, synthetic, dev, plan, reps=5):
     return {"nside": plan.nside, "lmax": L, "maps": B, "eps": plan.eps,
             "fwd_bwd_ms": round(ms, 3), "fwd_bwd_ms_per_map": round(ms / B, 3),
             "directional_derivative_rel_err": abs(float(fd) - dd) / abs(dd)}
+
+
+def regenerated_residual(sh, synthetic, dev, plan, B=8, reps=5):
+    """The same compressed operator (Nside=1024, L=2048, eps=1e-10) with its
+    residual blocks regenerated by the recurrence from two start values per
+    (block, column) instead of stored: synthesis of B maps against the stored
+    plan, plan memory of both, and the largest relative RMS difference."""
+    import torch
+    L = plan.lmax
+    regen = sh.Plan(plan.nside, L, plan.eps, gpu_build=True, residual_recurrence=True)
+    a = torch.from_numpy(synthetic.gaussian_alm(L, B, seed=4400)).to(dev)
+    m0 = torch.empty((B, plan.npix), dtype=torch.float64, device=dev)
+    m1 = torch.empty_like(m0)
+    ms_stored = event_ms(lambda: plan.synthesize(a, out=m0), reps) / B
+    ms_regen = event_ms(lambda: regen.synthesize(a, out=m1), reps) / B
+    diff = max(float(((m1[b] - m0[b]).norm() / m0[b].norm()).item()) for b in range(B))
+    s0, s1 = plan.stats(), regen.stats()
+    regen.close()
+    return {"nside": plan.nside, "lmax": L, "maps": B, "eps": plan.eps,
+            "stored_ms_per_map": round(ms_stored, 3), "regenerated_ms_per_map": round(ms_regen, 3),
+            "stored_plan_gb": round(s0["plan_device_bytes"] / 1e9, 3),
+            "regenerated_plan_gb": round(s1["plan_device_bytes"] / 1e9, 3),
+            "n_rstored": s0["n_rstored"], "n_rgen": s1["n_rgen"], "max_rel_rms_vs_stored": diff}
 
 
 def polarised_synthesis(sh, synthetic, dev, reps=5):

@@ -81,6 +81,14 @@ typedef struct {
     int spin;          /* 0: scalar plan; 2: polarised (spin-2) plan, whose transforms
                           are shtb_synthesize_spin (the spin-weighted transforms of
                           Sec. 5, by compressing the spin-weighted operators)      */
+    int residual_recurrence; /* compressed scalar plans: 0 (default) stores each
+                          residual block R = Lambda[I, skeleton] (Sec. 3.2); 1 keeps
+                          two start values per (block, column) instead and
+                          regenerates R during synthesis by the jump-two recurrence
+                          of Eq. (three-term), as Sec. 3.3 does to save memory.  Such
+                          plans serve synthesis only (shtb_synthesize,
+                          shtb_synthesize_host); adjoint, analysis and batches
+                          return SHTB_ENOTSUP.  Needs eps > 0 and spin = 0.      */
 } shtb_plan_opts;
 
 /* Plan statistics (algorithmic counts; used for roofline accounting). */
@@ -110,6 +118,9 @@ typedef struct {
     int from_cache;                 /* 1: the plan was read from a plan file          */
     int spin;                       /* 0 scalar, 2 polarised; for a polarised plan the
                                        element and byte counts cover both operators  */
+    long long n_rgen;               /* residual-block elements regenerated by the
+                                       recurrence per synthesis (residual_recurrence
+                                       plans; n_rstored is then 0)                    */
 } shtb_plan_stats_t;
 
 /*
@@ -506,6 +517,20 @@ int shtb_test_host_butterfly(int nside, int lmax, double eps, int m, int t, int 
  */
 int shtb_test_host_interp(int nside, int lmax, double eps, int m, int t, int leaf_cols, const double *a,
                           double *q_interp, double *q_exact, long long *info);
+
+/*
+ * Private host-only check (no GPU) of residual_recurrence plans: compresses
+ * chain (m, t) as a plan of tolerance eps does, then regenerates every
+ * residual block R = Lambda[I, skeleton] from the per-column recurrence
+ * starts such a plan keeps (the jump-two recurrence of Eq. three-term,
+ * stepped as the kernel steps it, times sigma) and compares it with the
+ * stored block.  *max_rel: largest |R_regen - R_stored| relative to the
+ * largest |R| of the same column.  info[0..3] = {blocks, elements, elements
+ * zero on one side only (the 1e-30 crop), chain depth}.
+ * Errors: SHTB_EINVAL, SHTB_ENOTSUP.
+ */
+int shtb_test_host_rec_blocks(int nside, int lmax, double eps, int m, int t, int leaf_cols, double *max_rel,
+                              long long *info);
 
 /*
  * Host-only check of the spin-weighted functions of spin plans (the

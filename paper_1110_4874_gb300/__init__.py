@@ -44,7 +44,8 @@ class ShtbError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("leaf_cols", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("rho", ctypes.c_double), ("nthreads", ctypes.c_int), ("device", ctypes.c_int),
-                ("cache_dir", ctypes.c_char_p), ("gpu_build", ctypes.c_int), ("spin", ctypes.c_int)]
+                ("cache_dir", ctypes.c_char_p), ("gpu_build", ctypes.c_int), ("spin", ctypes.c_int),
+                ("residual_recurrence", ctypes.c_int)]
 
 
 class PlanStats(ctypes.Structure):
@@ -57,7 +58,7 @@ class PlanStats(ctypes.Structure):
                 ("recurrence_flops", ctypes.c_double), ("phi_flops_per_map", ctypes.c_double),
                 ("build_seconds", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
                 ("n_ident", ctypes.c_longlong), ("depth_hist", ctypes.c_int * 16),
-                ("from_cache", ctypes.c_int), ("spin", ctypes.c_int)]
+                ("from_cache", ctypes.c_int), ("spin", ctypes.c_int), ("n_rgen", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "depth_hist"}
@@ -127,6 +128,7 @@ SIGNATURES = {
     "shtb_test_host_spin_column": (_I, [_I, _I, _I, _I, _I, _DP]),
     "shtb_test_host_interp": (_I, [_I, _I, _D, _I, _I, _I, _DP, _DP, _DP,
                                    ctypes.POINTER(ctypes.c_longlong)]),
+    "shtb_test_host_rec_blocks": (_I, [_I, _I, _D, _I, _I, _I, _DP, ctypes.POINTER(ctypes.c_longlong)]),
     "shtb_struct_sizes": (_I, [ctypes.POINTER(_I)] * 4),
 }
 
@@ -201,9 +203,11 @@ def shtb_last_error_message() -> str:
 def shtb_plan_create(nside: int, lmax: int, eps: float = 0.0, leaf_cols: int = 32,
                      max_depth: int = -1, rho: float = 0.0, nthreads: int = 0,
                      device: int = -1, cache_dir: str | None = None,
-                     spin: int = 0, gpu_build: bool = False) -> ctypes.c_void_p:
+                     spin: int = 0, gpu_build: bool = False,
+                     residual_recurrence: bool = False) -> ctypes.c_void_p:
     opts = shtb_plan_opts_init()
     opts.spin = spin
+    opts.residual_recurrence = 1 if residual_recurrence else 0
     opts.gpu_build = 1 if gpu_build else 0
     opts.leaf_cols, opts.max_depth, opts.rho = leaf_cols, max_depth, rho
     opts.nthreads, opts.device = nthreads, device
@@ -499,6 +503,18 @@ def shtb_test_host_interp(nside: int, lmax: int, eps: float, m: int, t: int, a, 
     return q, qe, dict(zip(keys, list(info)))
 
 
+def shtb_test_host_rec_blocks(nside: int, lmax: int, eps: float, m: int, t: int, leaf_cols: int = 32):
+    """Residual blocks of one (m, parity) chain regenerated on the host from
+    the recurrence starts a residual_recurrence plan keeps, against the
+    stored blocks: (largest error relative to the column's largest element,
+    {blocks, elements, crop mismatches, depth})."""
+    err = ctypes.c_double()
+    info = (ctypes.c_longlong * 4)()
+    _check(lib().shtb_test_host_rec_blocks(nside, lmax, float(eps), m, t, leaf_cols, ctypes.byref(err), info),
+           "shtb_test_host_rec_blocks")
+    return err.value, dict(zip(("blocks", "elements", "crop_mismatch", "depth"), list(info)))
+
+
 def shtb_test_host_spin_column(nside: int, lmax: int, m: int, s: int, r: int):
     """s_lambda_lm (s = +-2) at half-ring r for l = m..lmax, as spin plans build it."""
     import numpy as np
@@ -586,6 +602,8 @@ class Plan:
     one.  Keyword options are those of shtb_plan_create: spin=2 for a
     polarised plan (synthesize_spin / adjoint_spin / analyze_spin),
     gpu_build=True to batch the plan's decompositions on the GPU,
+    residual_recurrence=True to keep recurrence start values instead of the
+    residual blocks (synthesis only; less plan memory, more FP64 work),
     cache_dir=... to keep plan files, and leaf_cols, max_depth, rho,
     nthreads, device."""
 

@@ -242,6 +242,7 @@ int shtb_plan_opts_init(shtb_plan_opts *o)
     o->cache_dir = nullptr;
     o->gpu_build = 0;
     o->spin = 0;
+    o->residual_recurrence = 0;
     return SHTB_OK;
 }
 
@@ -333,6 +334,8 @@ int shtb_plan_create(int nside, int lmax, double eps, const shtb_plan_opts *opts
     shtb_plan_opts_init(&o);
     if (opts) o = *opts;
     if (o.spin != 0 && o.spin != 2) return shtb_fail(SHTB_EINVAL, "spin must be 0 (scalar) or 2 (polarised)");
+    if (o.residual_recurrence && (!(eps > 0) || o.spin != 0))
+        return shtb_fail(SHTB_ENOTSUP, "residual_recurrence needs a compressed scalar plan (eps > 0, spin 0)");
     int dev = o.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) return shtb_fail(SHTB_ECUDA, "no CUDA device");

@@ -650,6 +650,10 @@ int shtb_batch_create(const shtb_request *reqs, int nreq, const shtb_batch_opts 
             delete b;
             return shtb_fail(SHTB_ENOTSUP, "batches need compressed scalar plans (eps > 0)");
         }
+        if (r.plan->bf->rec) {
+            delete b;
+            return shtb_fail(SHTB_ENOTSUP, "batches need plans that store their residual blocks");
+        }
         if (r.plan->device != dev) {
             delete b;
             return shtb_fail(SHTB_EMISMATCH, "request " + std::to_string(i) + " uses a plan of another device");

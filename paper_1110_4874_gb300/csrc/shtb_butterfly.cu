@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "shtb_bf_items.cuh"
+#include "shtb_bf_regen.cuh"
 #include "shtb_butterfly.h"
 
 namespace {
@@ -64,17 +65,24 @@ struct StageTile {
         : T(nmaps >= kStageTile ? 1 : kStageTile / nmaps), MB(nmaps < kStageTile ? nmaps : kStageTile) {}
 };
 
-// ai[idx][b] = a_lm[b][idx] (Im a_l0 = 0, Sec. 2.1: idx <= L is m = 0)
+// ai[idx][b] = a_lm[b][idx] (Im a_l0 = 0, Sec. 2.1: idx <= L is m = 0), times
+// sigma_lm when sig is non-null (plans that regenerate R by the rescaled
+// recurrence, Ptilde = sigma V)
+__device__ __forceinline__ double2 staged(double2 a, long long i, long long L, const RecCoef *sig)
+{
+    const double s = sig ? sig[i].sig : 1.0;
+    return sig ? make_double2(a.x * s, i <= L ? 0.0 : a.y * s) : make_double2(a.x, i <= L ? 0.0 : a.y);
+}
+
 __global__ void __launch_bounds__(256) bf_interleave_kernel(PlanView v, const double2 *__restrict__ alm,
-                                                            double2 *__restrict__ ai, int nmaps)
+                                                            double2 *__restrict__ ai, int nmaps,
+                                                            const RecCoef *__restrict__ sig)
 {
     __shared__ double2 tile[2 * kStageTile];
     const long long nalm = v.nalm, L = v.lmax;
     if (nmaps == 1) {
-        for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nalm; i += 256LL * gridDim.x) {
-            const double2 a = alm[i];
-            ai[i] = make_double2(a.x, i <= L ? 0.0 : a.y);
-        }
+        for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nalm; i += 256LL * gridDim.x)
+            ai[i] = staged(alm[i], i, L, sig);
         return;
     }
     const StageTile st(nmaps);
@@ -89,8 +97,7 @@ __global__ void __launch_bounds__(256) bf_interleave_kernel(PlanView v, const do
             __syncthreads();
             for (int e = threadIdx.x; e < nt * mb; e += blockDim.x) {
                 const int t = e / mb, b = e - t * mb;
-                const double2 a = tile[b * (st.T + 1) + t];
-                ai[(size_t)(i0 + t) * nmaps + b0 + b] = make_double2(a.x, i0 + t <= L ? 0.0 : a.y);
+                ai[(size_t)(i0 + t) * nmaps + b0 + b] = staged(tile[b * (st.T + 1) + t], i0 + t, L, sig);
             }
             __syncthreads();
         }
@@ -156,6 +163,22 @@ bf_level_kernel(const BfItem *__restrict__ items, int nitems, int L, int nhalf, 
     shtb_dev::bf_level_item<NB, false, RING ? 1 : 0>(items[w], L, nhalf, ints, dbl, uin, uout, qt, scr, lane);
 }
 
+// regenerated residual blocks (residual_recurrence plans), one per warp
+template <int NB>
+__global__ void __launch_bounds__(32 * kBfWarps)
+bf_r_rec_kernel(PlanView v, const BfRItem *__restrict__ items, int nitems, const RecStart *__restrict__ rs,
+                const int *__restrict__ ints, const double2 *__restrict__ ai, int nmaps, int b0,
+                double *__restrict__ ubuf0, double *__restrict__ ubuf1, const int *__restrict__ depth_par,
+                double *__restrict__ qt)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kBfWarps + (threadIdx.x >> 5);
+    if (w >= nitems) return;
+    const BfRItem it = items[w];
+    double *ubuf = depth_par[it.m * 2 + it.t] ? ubuf1 : ubuf0;
+    shtb_dev::bf_r_rec_item<NB, false>(it, v, rs, ints, ai, nmaps, b0, ubuf, qt, lane);
+}
+
 // residual blocks of one map group (maps b0 .. b0+NB-1 of ai)
 template <int NB>
 int launch_r(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double *u0, double *u1,
@@ -163,6 +186,14 @@ int launch_r(const shtb_plan_s *p, const double2 *ai, int nmaps, int b0, double 
 {
     const BfPlanDev &bf = *p->bf;
     if (bf.n_ritems == 0) return SHTB_OK;
+    if (bf.rec) {
+        const unsigned grid = (unsigned)((bf.n_ritems + kBfWarps - 1) / kBfWarps);
+        bf_r_rec_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(p->view, bf.ritems, bf.n_ritems, bf.rstart, bf.ints,
+                                                            ai, nmaps, b0, u0, u1, bf.depth_parity, qt);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+        return SHTB_OK;
+    }
     const long long warps = (bf.n_ritems + items_per_warp_residual<NB>() - 1) / items_per_warp_residual<NB>();
     const unsigned grid = (unsigned)((warps + kBfWarps - 1) / kBfWarps);
     bf_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(p->view, bf.ritems, bf.n_ritems, bf.ints, bf.dbl, ai,
@@ -496,7 +527,8 @@ int launch_bf_synth(const shtb_plan_s *p, const double2 *alm, double2 *ai, void 
     const size_t qt_map = (size_t)4 * p->nhalf * (p->lmax + 1);
     auto qt_of = [&](int b0) { return qt_out ? qt_out + (size_t)b0 * qt_map : qt_ws; };
     const int ev = profile_begin(const_cast<shtb_plan_s *>(p), st);
-    bf_interleave_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, alm, ai, nmaps);
+    bf_interleave_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, alm, ai, nmaps,
+                                                               p->bf->rec ? p->view.coef : nullptr);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     profile_end(const_cast<shtb_plan_s *>(p), st, 4, ev);
@@ -526,7 +558,8 @@ int launch_bf_synth_to_host(shtb_plan_s *p, const double2 *alm, double2 *ai, voi
     double *u0 = (double *)ws;
     double *u1 = u0 + (size_t)bf.u_entries * entry;
     double *qt = u1 + (size_t)bf.u_entries * entry;
-    bf_interleave_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, alm, ai, nmaps);
+    bf_interleave_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, alm, ai, nmaps,
+                                                               p->bf->rec ? p->view.coef : nullptr);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     for (int b0 = 0; b0 < nmaps;) {
@@ -558,6 +591,7 @@ int launch_bf_synth_to_host(shtb_plan_s *p, const double2 *alm, double2 *ai, voi
 int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
                       int nmaps, cudaStream_t st)
 {
+    if (p->bf->rec) return shtb_fail(SHTB_ENOTSUP, "adjoint of a plan that regenerates its residual blocks");
     const BfPlanDev &bf = *p->bf;
     const size_t entry = 16;
     double *u0 = (double *)ws;

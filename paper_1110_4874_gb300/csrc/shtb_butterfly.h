@@ -41,6 +41,7 @@ struct BfRLocal {
     bool to_rings = false;           // depth 0: outputs go straight to q^t rings
     long long out_off = 0;           // u entry offset (within the chain's region)
     std::vector<int> rings;
+    std::vector<int> cols;           // the half-ring of each column
     std::vector<double> data;        // nrows x k, row-major
 };
 
@@ -78,8 +79,18 @@ struct BfRItem {
     int m, t;
     int j0, nrows, k;
     int to_rings;                    // 1: write q^t entries listed at idx_off
-    long long data_off;              // doubles: nrows x k row-major
+    long long data_off;              // doubles: nrows x k row-major (stored R)
     long long out_off;               // u entry offset (to_rings = 0) or int offset of entry list
+    long long rs_off;                // first of the block's k RecStart (regenerated R)
+};
+
+// Start of the jump-two recurrence for one column of a residual block, in
+// plans that regenerate R (Eq. three-term; Ptilde = sigma V): the column's
+// half-ring, the first block row at or past the 1e-30 crop (nrows: the
+// column is zero in this block), and V at that row and the next.
+struct RecStart {
+    int ring, start;
+    double v0, v1;
 };
 
 struct BfItem {
@@ -113,10 +124,18 @@ struct BfPlanDev {
     const int *ints = nullptr;
     const double *dbl = nullptr;
     const int *depth_parity = nullptr;   // per chain (m*2 + t): depth % 2 (u buffer of its R output)
+    const RecStart *rstart = nullptr;    // regenerated R: one per (block, column)
+    bool rec = false;                    // R regenerated by the recurrence, not stored
+    long long n_rgen = 0;
     long long u_entries = 0;         // entries per u buffer
     long long qt_entries = 0;        // (L+1) * 2 * nhalf
     long long n_dense = 0, n_r = 0, n_ident = 0;
 };
+
+namespace shtb {
+RecStart block_column_start(int n, int t, int j0, int nrows, int ring, double x, bool sform, const RecCoef *cf,
+                            int js, double2 vs);
+}
 
 // Builds the compressed operator of a plan (eps > 0) and uploads it.
 int shtb_build_butterfly(shtb_plan_s *p);

@@ -41,6 +41,9 @@ void legendre_column(int L, int m, const HalfRing &h, DD cm, const std::vector<d
 // Spin-weighted s_lambda_lm (s = +-2) at one half-ring for l = m..L (zero
 // below l = 2), by the Wigner recurrence in l; out has L - m + 1 slots.
 void spin_column(int L, int m, int s, const HalfRing &h, DD cm, double *out);
+// Lambda^{m,t} of both parities of one m (column-major, n_t rows x Z columns)
+void build_lambda(int L, int m, int Z, const std::vector<HalfRing> &hr, DD cm, std::vector<double> &lam0,
+                  std::vector<double> &lam1);
 
 constexpr double kCrop = 1e-30;   // Appendix: values below 1e-30 are neglected
 

@@ -15,6 +15,7 @@
 #include <thread>
 #include <vector>
 
+#include "shtb_butterfly.h"
 #include "shtb_dd.h"
 #include "shtb_internal.h"
 #include "shtb_plan_detail.h"
@@ -940,6 +941,74 @@ extern "C" int shtb_test_host_recurrence(int nside, int lmax, int m, int r, doub
             cur = nxt;
         }
     }
+    return SHTB_OK;
+}
+
+// Private host-only check of regenerated residual blocks (no GPU): builds
+// chain (m, t) of a compressed plan, then every residual block's R again from
+// its per-column recurrence starts (the start records a residual_recurrence
+// plan keeps, stepped as the kernel steps them, times sigma) and compares
+// them with the stored blocks.  info[0..3] = {blocks, regenerated elements,
+// elements that differ in the crop (one side zero), depth}; *max_rel = the
+// largest |R_regen - R_stored| over the largest |R| of the block's column.
+extern "C" int shtb_test_host_rec_blocks(int nside, int lmax, double eps, int m, int t, int leaf_cols,
+                                         double *max_rel, long long *info)
+{
+    if (nside < 1 || lmax < 0 || m < 0 || m > lmax || t < 0 || t > 1 || !(eps > 0) || leaf_cols < 1 ||
+        leaf_cols > shtb::kMaxCand || !max_rel || !info)
+        return shtb_fail(SHTB_EINVAL, "bad arguments");
+    const int Z = 2 * nside, n = chain_len(lmax, m, t);
+    if (n < 1) return shtb_fail(SHTB_EINVAL, "empty chain");
+    std::vector<HalfRing> hr(Z);
+    for (int r = 0; r < Z; ++r) hr[r] = half_ring(nside, r + 1);
+    const std::vector<DD> cm = diag_norms(lmax);
+    std::vector<double> lam0, lam1;
+    shtb::build_lambda(lmax, m, Z, hr, cm[m], lam0, lam1);
+    shtb::BfParams prm;
+    prm.eps = eps;
+    prm.leaf_cols = leaf_cols;
+    shtb::BfChain ch;
+    int rc = shtb::compress_chain(t ? lam1.data() : lam0.data(), n, Z, prm, &ch);
+    if (rc) return rc;
+    std::vector<RecCoef> cf(lmax - m + 1);
+    build_coefficients(lmax, m, cf.data());
+    const std::vector<double> b = one_step_coefs(lmax, m);
+    *max_rel = 0.0;
+    long long nb = 0, ne = 0, ncrop = 0;
+    for (const auto &rb : ch.rblocks) {
+        ++nb;
+        for (int s = 0; s < rb.k; ++s) {
+            const int r = rb.cols[s];
+            const HalfRing &h = hr[r];
+            const bool sform = h.s2 < 0.5;
+            const double x = sform ? -h.s2 : h.z2;
+            int js[2];
+            double2 vs[2];
+            chain_starts(lmax, m, h, cm[m], b, cf.data(), js, vs);
+            const RecStart st = shtb::block_column_start(n, t, rb.j0, rb.nrows, r, x, sform, cf.data(), js[t], vs[t]);
+            double cmax = 0.0;
+            for (int j = 0; j < rb.nrows; ++j) cmax = std::max(cmax, std::fabs(rb.data[(size_t)j * rb.k + s]));
+            double cur = st.start == 0 ? st.v0 : 0.0, prev = 0.0;
+            for (int j = 0; j < rb.nrows; ++j) {
+                const int dl = t + 2 * (rb.j0 + j);
+                const double regen = cf[dl].sig * cur, stored = rb.data[(size_t)j * rb.k + s];
+                if ((regen == 0.0) != (stored == 0.0)) ++ncrop;
+                if (cmax > 0) *max_rel = std::max(*max_rel, std::fabs(regen - stored) / cmax);
+                ++ne;
+                const RecCoef &c = cf[dl];
+                const double w = std::fma(c.mu, x, sform ? c.cs : c.cz);
+                double nxt = std::fma(w, cur, -prev);
+                if (j == st.start) nxt = st.v1;
+                if (j + 1 == st.start) nxt = st.v0;
+                prev = cur;
+                cur = nxt;
+            }
+        }
+    }
+    info[0] = nb;
+    info[1] = ne;
+    info[2] = ncrop;
+    info[3] = ch.depth;
     return SHTB_OK;
 }
 

@@ -176,3 +176,19 @@ def test_interpolation_variant_stores_more_than_the_butterfly():
             _, _, info = sh.shtb_test_host_interp(nside, lmax, 1e-10, m, t, a)
             two_step = info["roots_butterfly"] + min(info["interp_butterfly"], info["interp_hierarchical"])
             assert two_step > info["rings_butterfly"], (m, t, info)
+
+
+@pytest.mark.parametrize("nside,lmax,eps,m,t,bound", [
+    (64, 128, 1e-10, 0, 0, 1e-13), (256, 512, 1e-12, 200, 1, 1e-13),
+    (512, 1024, 1e-10, 0, 1, 2e-12), (512, 1024, 1e-10, 900, 1, 1e-13),
+    (2048, 4096, 1e-10, 0, 0, 2e-11), (2048, 4096, 1e-10, 1000, 1, 2e-12)])
+def test_regenerated_residual_blocks_match_the_stored_ones(nside, lmax, eps, m, t, bound):
+    """Residual blocks rebuilt from the two recurrence start values per
+    (block, column) that residual_recurrence plans keep (Eq. three-term,
+    stepped as the kernel steps it) reproduce the stored blocks: same 1e-30
+    crop, and the FP64 recurrence's rounding only (it grows with the chain
+    length, to ~6e-12 of a column's largest value for m = 0 at L = 4096)."""
+    err, info = sh.shtb_test_host_rec_blocks(nside, lmax, eps, m, t)
+    assert info["blocks"] > 0 and info["elements"] > 0
+    assert info["crop_mismatch"] == 0
+    assert err <= bound
