@@ -85,10 +85,10 @@ typedef struct {
                           residual block R = Lambda[I, skeleton] (Sec. 3.2); 1 keeps
                           two start values per (block, column) instead and
                           regenerates R during synthesis by the jump-two recurrence
-                          of Eq. (three-term), as Sec. 3.3 does to save memory.  Such
-                          plans serve synthesis only (shtb_synthesize,
-                          shtb_synthesize_host); adjoint, analysis and batches
-                          return SHTB_ENOTSUP.  Needs eps > 0 and spin = 0.      */
+                          of Eq. (three-term), as Sec. 3.3 does to save memory (and
+                          its transpose in the adjoint).  Batches (shtb_batch_create)
+                          return SHTB_ENOTSUP on such plans.  Needs eps > 0 and
+                          spin = 0, else SHTB_ENOTSUP.                            */
 } shtb_plan_opts;
 
 /* Plan statistics (algorithmic counts; used for roofline accounting). */

@@ -603,7 +603,7 @@ class Plan:
     polarised plan (synthesize_spin / adjoint_spin / analyze_spin),
     gpu_build=True to batch the plan's decompositions on the GPU,
     residual_recurrence=True to keep recurrence start values instead of the
-    residual blocks (synthesis only; less plan memory, more FP64 work),
+    residual blocks (less plan memory, more FP64 work; no batches),
     cache_dir=... to keep plan files, and leaf_cols, max_depth, rho,
     nthreads, device."""
 

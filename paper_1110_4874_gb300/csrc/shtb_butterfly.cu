@@ -442,15 +442,40 @@ bf_adj_r_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
     }
 }
 
+// adjoint of regenerated residual blocks, one (chain, row interval) per warp
+template <int NB>
+__global__ void __launch_bounds__(32 * kBfWarps)
+bf_adj_r_rec_kernel(PlanView v, const BfRGroup *__restrict__ groups, int ngroups,
+                    const BfRItem *__restrict__ ritems, const RecStart *__restrict__ rs,
+                    const int *__restrict__ ints, const double *__restrict__ u0, const double *__restrict__ u1,
+                    const int *__restrict__ depth_par, const double2 *__restrict__ g, int nmaps, int b0,
+                    double2 *__restrict__ aacc)
+{
+    extern __shared__ double smem_rec[];     // [kBfWarps][32 x 33 + 32 x C]
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int w = blockIdx.x * kBfWarps + wib;
+    if (w >= ngroups) return;
+    const BfRGroup gr = groups[w];
+    const double *ubuf = depth_par[gr.m * 2 + gr.t] ? u1 : u0;
+    shtb_dev::bf_adj_r_rec_group<NB>(gr, v, ritems, rs, ints, ubuf, reinterpret_cast<const double *>(g), nmaps, b0,
+                                     reinterpret_cast<double *>(aacc),
+                                     smem_rec + (size_t)wib * (32 * 33 + 32 * 2 * NB), lane);
+}
+
 // alm[b][idx] = c_m aacc[idx][b] (c_0 = 1 with Im a_l0 = 0, c_m = 2), the
-// transposed staging of bf_interleave_kernel
+// transposed staging of bf_interleave_kernel; times sigma_lm when sig is
+// non-null (plans that regenerate R: the residual adjoint sums V, not
+// Ptilde = sigma V)
 __global__ void __launch_bounds__(256) bf_finish_kernel(PlanView v, const double2 *__restrict__ aacc,
-                                                        double2 *__restrict__ alm, int nmaps)
+                                                        double2 *__restrict__ alm, int nmaps,
+                                                        const RecCoef *__restrict__ sig)
 {
     __shared__ double2 tile[2 * kStageTile];
     const long long nalm = v.nalm, L = v.lmax;
-    auto scaled = [L](double2 a, long long idx) {
-        return idx <= L ? make_double2(a.x, 0.0) : make_double2(2.0 * a.x, 2.0 * a.y);
+    auto scaled = [L, sig](double2 a, long long idx) {
+        const double cs = (idx <= L ? 1.0 : 2.0) * (sig ? sig[idx].sig : 1.0);
+        return idx <= L ? make_double2(sig ? a.x * cs : a.x, 0.0)
+                        : make_double2(sig ? cs * a.x : 2.0 * a.x, sig ? cs * a.y : 2.0 * a.y);
     };
     if (nmaps == 1) {
         for (long long i = blockIdx.x * 256LL + threadIdx.x; i < nalm; i += 256LL * gridDim.x)
@@ -495,7 +520,17 @@ int run_adj_group(const shtb_plan_s *p, const double2 *g, int nmaps, int b0, dou
         SHTB_CUDA_TRY(cudaGetLastError());
         ++p->launches;
     }
-    if (bf.n_rgroups > 0) {
+    if (bf.n_rgroups > 0 && bf.rec) {
+        const unsigned grid = (unsigned)((bf.n_rgroups + kBfWarps - 1) / kBfWarps);
+        const size_t smem = sizeof(double) * kBfWarps * (32 * 33 + 32 * 2 * NB);
+        SHTB_CUDA_TRY(cudaFuncSetAttribute(bf_adj_r_rec_kernel<NB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bf_adj_r_rec_kernel<NB><<<grid, 32 * kBfWarps, smem, st>>>(p->view, bf.rgroups, bf.n_rgroups, bf.ritems,
+                                                                   bf.rstart, bf.ints, u0, u1, bf.depth_parity,
+                                                                   g, nmaps, b0, aacc);
+        SHTB_CUDA_TRY(cudaGetLastError());
+        ++p->launches;
+    } else if (bf.n_rgroups > 0) {
         const unsigned grid = (unsigned)((bf.n_rgroups + kBfWarps - 1) / kBfWarps);
         bf_adj_r_kernel<NB><<<grid, 32 * kBfWarps, 0, st>>>(p->view, bf.rgroups, bf.n_rgroups, bf.ritems,
                                                             bf.ints, bf.dbl, u0, u1, bf.depth_parity, g,
@@ -591,7 +626,6 @@ int launch_bf_synth_to_host(shtb_plan_s *p, const double2 *alm, double2 *ai, voi
 int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, void *ws, double2 *alm,
                       int nmaps, cudaStream_t st)
 {
-    if (p->bf->rec) return shtb_fail(SHTB_ENOTSUP, "adjoint of a plan that regenerates its residual blocks");
     const BfPlanDev &bf = *p->bf;
     const size_t entry = 16;
     double *u0 = (double *)ws;
@@ -605,7 +639,8 @@ int launch_bf_adjoint(const shtb_plan_s *p, const double2 *g, double2 *aacc, voi
         else { rc = run_adj_group<1>(p, g, nmaps, b0, u0, u1, aacc, st); b0 += 1; }
         if (rc) return rc;
     }
-    bf_finish_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, aacc, alm, nmaps);
+    bf_finish_kernel<<<stage_grid(p, nmaps), 256, 0, st>>>(p->view, aacc, alm, nmaps,
+                                                           p->bf->rec ? p->view.coef : nullptr);
     SHTB_CUDA_TRY(cudaGetLastError());
     ++p->launches;
     return SHTB_OK;
