@@ -578,8 +578,9 @@ def differentiation(sh, synthetic, dev, plan, reps=5):
 def regenerated_residual(sh, synthetic, dev, plan, B=8, reps=5):
     """The same compressed operator (Nside=1024, L=2048, eps=1e-10) with its
     residual blocks regenerated by the recurrence from two start values per
-    (block, column) instead of stored: synthesis of B maps against the stored
-    plan, plan memory of both, and the largest relative RMS difference."""
+    (block, column) instead of stored: synthesis and adjoint of B maps against
+    the stored plan, plan memory of both, and the largest relative RMS
+    differences."""
     import torch
     L = plan.lmax
     regen = sh.Plan(plan.nside, L, plan.eps, gpu_build=True, residual_recurrence=True)
@@ -589,13 +590,20 @@ def regenerated_residual(sh, synthetic, dev, plan, B=8, reps=5):
     ms_stored = event_ms(lambda: plan.synthesize(a, out=m0), reps) / B
     ms_regen = event_ms(lambda: regen.synthesize(a, out=m1), reps) / B
     diff = max(float(((m1[b] - m0[b]).norm() / m0[b].norm()).item()) for b in range(B))
+    a0 = torch.empty_like(a)
+    a1 = torch.empty_like(a)
+    ms_adj_stored = event_ms(lambda: plan.adjoint(m0, out=a0), reps) / B
+    ms_adj_regen = event_ms(lambda: regen.adjoint(m0, out=a1), reps) / B
+    adiff = max(float(((a1[b] - a0[b]).norm() / a0[b].norm()).item()) for b in range(B))
     s0, s1 = plan.stats(), regen.stats()
     regen.close()
     return {"nside": plan.nside, "lmax": L, "maps": B, "eps": plan.eps,
             "stored_ms_per_map": round(ms_stored, 3), "regenerated_ms_per_map": round(ms_regen, 3),
             "stored_plan_gb": round(s0["plan_device_bytes"] / 1e9, 3),
             "regenerated_plan_gb": round(s1["plan_device_bytes"] / 1e9, 3),
-            "n_rstored": s0["n_rstored"], "n_rgen": s1["n_rgen"], "max_rel_rms_vs_stored": diff}
+            "n_rstored": s0["n_rstored"], "n_rgen": s1["n_rgen"], "max_rel_rms_vs_stored": diff,
+            "adjoint_stored_ms_per_map": round(ms_adj_stored, 3),
+            "adjoint_regenerated_ms_per_map": round(ms_adj_regen, 3), "adjoint_max_rel_rms_vs_stored": adiff}
 
 
 def polarised_synthesis(sh, synthetic, dev, reps=5):
