@@ -241,7 +241,8 @@ def run_ours(args, rank, world, dist):
     try:
         try:
             plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols, gpu_build=not args.host_build,
-                           nthreads=build_threads(world, not args.host_build))
+                           nthreads=build_threads(world, not args.host_build),
+                           residual_recurrence=args.residual_recurrence)
         except sh.ShtbError as e:
             # the GPU builder needs pinned staging per host worker; where the
             # host cannot give it (SHTB_ENOMEM), the same plan is built with
@@ -250,7 +251,8 @@ def run_ours(args, rank, world, dist):
                 raise
             built_on = f"host (GPU builder: {e})"
             plan = sh.Plan(N, L, eps_plan, leaf_cols=args.leaf_cols,
-                           nthreads=build_threads(world, False))
+                           nthreads=build_threads(world, False),
+                           residual_recurrence=args.residual_recurrence)
     except sh.ShtbError as e:
         if e.code != sh.SHTB_ENOTSUP or eps_plan <= 0:
             raise
@@ -345,7 +347,9 @@ def run_ours(args, rank, world, dist):
     if st["compressed"]:
         per_step = {   # kernel -> (algorithmic flops per step, ms per step)
             "bf_level_kernel": (B * 4.0 * st["n_dense"], stages["bf_levels"] / ncall),
-            "bf_r_kernel": (B * 4.0 * st["n_rstored"], stages["bf_residual"] / ncall),
+            # stored blocks: 4B flop per element; regenerated: 4B + 4 (one recurrence step)
+            "bf_r_kernel": (B * 4.0 * st["n_rstored"] + (4.0 * B + 4.0) * st["n_rgen"],
+                            stages["bf_residual"] / ncall),
         }
     else:
         per_step = {"legendre_synth_kernel": (sum(4.0 * st["n_recurrence"] * (1 + g) for g in groups),
@@ -665,12 +669,15 @@ def workload_config(args, world):
     N, L, B = args.nside, args.lmax, args.nmaps
     gb = lambda x: round(x / 1e9, 2)  # noqa: E731
     a_bytes, m_bytes = 16 * B * (L + 1) * (L + 2) / 2, 8 * B * 12 * N * N
-    return {"workload": f"HEALPix synthesis Nside={N} L={L} batch of {B} maps",
-            "nside": N, "lmax": L, "nmaps": B, "eps": args.eps, "leaf_cols": args.leaf_cols,
-            "parallelism": f"replicas x{world}",
-            "l2": (f"a_lm {gb(a_bytes)} GB and maps {gb(m_bytes)} GB per step, "
-                   + ("both larger than the 129 MB L2" if min(a_bytes, m_bytes) > 129e6
-                      else "not both larger than the 129 MB L2"))}
+    cfg = {"workload": f"HEALPix synthesis Nside={N} L={L} batch of {B} maps",
+           "nside": N, "lmax": L, "nmaps": B, "eps": args.eps, "leaf_cols": args.leaf_cols,
+           "parallelism": f"replicas x{world}",
+           "l2": (f"a_lm {gb(a_bytes)} GB and maps {gb(m_bytes)} GB per step, "
+                  + ("both larger than the 129 MB L2" if min(a_bytes, m_bytes) > 129e6
+                     else "not both larger than the 129 MB L2"))}
+    if getattr(args, "residual_recurrence", False):
+        cfg["residual_blocks"] = "regenerated by the recurrence"
+    return cfg
 
 
 def run_reference(args):
@@ -711,6 +718,8 @@ def main():
     ap.add_argument("--cpu-rings", type=int, default=64, help="ring sample of the CPU baseline")
     ap.add_argument("--ref-rings", type=int, default=16, help="ring sample per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--residual-recurrence", action="store_true",
+                    help="plan that regenerates its residual blocks by the recurrence (less plan memory)")
     ap.add_argument("--host-build", action="store_true",
                     help="build the plan's interpolative decompositions on the host, not the GPU")
     ap.add_argument("--no-patterns", action="store_true",
